@@ -1,0 +1,261 @@
+"""FP64 CPU oracle for the Monte Carlo nodal stage of Probabilistic Domain
+Decomposition (Bernal & Acebron, Sec. 2 and Algorithm 1).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline load it; the library never does.  The arithmetic lives in
+``pdd_oracle.c`` (plain C, FP64, single-threaded); this module compiles it
+with gcc on first use and wraps it with ctypes and numpy.
+
+Parity pins (what fixes the oracle other than itself) are in
+``tests/test_oracle_*.py``.  Functions with no independent pin: none of the
+per-path arithmetic; the paper's Tables 2 and 3 are not reproduced (they need
+the subdomain FEM/RBF stage and the missing Fig. 1 geometry) -- parity
+unpinned for those, and they are out of scope.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pdd_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libpdd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# problem kinds (same numbering as the library's public enum, by definition of
+# the workloads, not by shared code)
+CFG0_2D, ANISO_2D, CUBE_3D, HARMONIC_2D = 0, 1, 2, 3
+CV_NONE, CV_GRID, CV_EXACT = 0, 1, 2
+GOBET_MENOZZI_C0 = 0.5826  # Algorithm 1, shrinkage constant as printed
+
+STAT_NAMES = [
+    "mean_phi", "var_phi", "mean_cv", "var_cv", "cov_phi_xi", "var_xi", "rho",
+    "se_phi", "se_cv", "vr", "pred_speedup", "mean_steps", "n_truncated", "mean_iso",
+    "mean_xi",
+]
+
+
+def build(force: bool = False) -> str:
+    """Compile pdd_oracle.c into libpdd_oracle.so (gcc, -O2, strict IEEE)."""
+    if force or not os.path.exists(_LIB_PATH) or (
+        os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    ):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+             "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        )
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        u32, u64, i64, dbl, i32 = (ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
+                                   ctypes.c_double, ctypes.c_int)
+        P = ctypes.c_void_p
+        lib.or_philox4x32_10.argtypes = [P, P, P]
+        lib.or_uniform.argtypes = [u32]
+        lib.or_uniform.restype = dbl
+        lib.or_normal.argtypes = [u64, u32, u32, u32, u64]
+        lib.or_normal.restype = dbl
+        lib.or_eval.argtypes = [i32, P, P]
+        lib.or_box_distance.argtypes = [i32, P, P, P]
+        lib.or_box_distance.restype = dbl
+        lib.or_box_project.argtypes = [i32, P, P]
+        lib.or_build_gradient.argtypes = [i32, i32, P, P]
+        lib.or_build_gradient.restype = i32
+        lib.or_grad_interp.argtypes = [i32, i32, P, P, P]
+        lib.or_nstat.restype = i32
+        lib.or_node_stats.argtypes = [i64, P, P, P, P, P, dbl, P]
+        lib.or_estimate_nodes.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, P, i64,
+                                          dbl, u64, u32, dbl, P, P, P, P, P, P]
+        lib.or_estimate_nodes.restype = i32
+        lib.or_sample_paths.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, P, P, P,
+                                        dbl, u64, u32, P, P, P]
+        lib.or_sample_paths.restype = i32
+        assert lib.or_nstat() == len(STAT_NAMES)
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block for one 128-bit counter and 64-bit key."""
+    lib = _load()
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib.or_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def uniform(x: int) -> float:
+    return _load().or_uniform(int(x))
+
+
+def normals(seed: int, tag: int, node: int, path: int, count: int, first: int = 0) -> np.ndarray:
+    lib = _load()
+    return np.array([lib.or_normal(seed, tag, node, path, first + i) for i in range(count)])
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_double * 3), ("sigma", (ctypes.c_double * 3) * 3),
+                ("A", (ctypes.c_double * 3) * 3), ("c", ctypes.c_double),
+                ("f", ctypes.c_double), ("u", ctypes.c_double), ("grad_u", ctypes.c_double * 3)]
+
+
+def coeffs(kind: int, x) -> dict:
+    """Coefficients b, sigma, A, c, f, u, grad u of a workload at point x."""
+    lib = _load()
+    xx = np.zeros(3)
+    xx[: len(x)] = x
+    o = Coeffs()
+    lib.or_eval(kind, _ptr(xx), ctypes.byref(o))
+    return {"b": np.array(o.b[:]), "sigma": np.array([r[:] for r in o.sigma]),
+            "A": np.array([r[:] for r in o.A]), "c": o.c, "f": o.f, "u": o.u,
+            "grad_u": np.array(o.grad_u[:])}
+
+
+def box_distance(dim: int, x):
+    lib = _load()
+    xx = np.zeros(3)
+    xx[:dim] = x[:dim]
+    ax, sd = ctypes.c_int(0), ctypes.c_int(0)
+    d = lib.or_box_distance(dim, _ptr(xx), ctypes.byref(ax), ctypes.byref(sd))
+    return d, ax.value, sd.value
+
+
+def box_project(dim: int, x) -> np.ndarray:
+    lib = _load()
+    xx = np.zeros(3)
+    xx[:dim] = x[:dim]
+    out = np.zeros(3)
+    lib.or_box_project(dim, _ptr(xx), _ptr(out))
+    return out[:dim]
+
+
+def build_gradient(dim: int, v: np.ndarray) -> np.ndarray:
+    """Gradient table (n^D, D) of grid values v (x index fastest)."""
+    lib = _load()
+    n = v.shape[0]
+    vv = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    grad = np.zeros(vv.size * dim)
+    rc = lib.or_build_gradient(dim, n, _ptr(vv), _ptr(grad))
+    if rc != 0:
+        raise ValueError("bad grid")
+    return grad
+
+
+def grad_interp(dim: int, n: int, grad: np.ndarray, x) -> np.ndarray:
+    lib = _load()
+    xx = np.zeros(3)
+    xx[:dim] = x[:dim]
+    out = np.zeros(3)
+    lib.or_grad_interp(dim, n, _ptr(grad), _ptr(xx), _ptr(out))
+    return out[:dim]
+
+
+def problem_dim(kind: int) -> int:
+    return 3 if kind == CUBE_3D else 2
+
+
+def default_max_steps(h: float) -> int:
+    """No cap in the paper; ceil(100 / h) steps, i.e. tau_h <= 100."""
+    return int(np.ceil(100.0 / h))
+
+
+def estimate_nodes(kind: int, nodes: np.ndarray, n_paths: int, h: float, seed: int = 1234,
+                   tag: int = 0, cv: int = CV_NONE, grad: np.ndarray | None = None,
+                   grid_n: int = 0, c0: float = GOBET_MENOZZI_C0, y_exp: bool = False,
+                   max_steps: int | None = None, kappa: float = 1.0, per_path: bool = True):
+    """Run Algorithm 1 for every (node, path) and return per-path arrays and
+    per-node statistics.  nodes: (n_nodes, D) float array (any float dtype;
+    the coordinates are used as given, in FP64)."""
+    lib = _load()
+    dim = problem_dim(kind)
+    nodes = np.asarray(nodes, dtype=np.float64).reshape(-1, dim)
+    n = nodes.shape[0]
+    xs = np.ascontiguousarray(nodes[:, 0])
+    ys = np.ascontiguousarray(nodes[:, 1])
+    zs = np.ascontiguousarray(nodes[:, 2]) if dim == 3 else None
+    if max_steps is None:
+        max_steps = default_max_steps(h)
+    tot = n * n_paths
+    phi = np.zeros(tot) if per_path else None
+    xi = np.zeros(tot) if per_path else None
+    steps = np.zeros(tot, dtype=np.int64) if per_path else None
+    iso = np.zeros(tot) if per_path else None
+    xstop = np.zeros(tot * 3) if per_path else None
+    stats = np.zeros(n * len(STAT_NAMES))
+    if grad is not None:
+        grad = np.ascontiguousarray(grad, dtype=np.float64)
+    rc = lib.or_estimate_nodes(kind, c0, int(y_exp), int(max_steps), cv, grid_n, _ptr(grad), n,
+                               _ptr(xs), _ptr(ys), _ptr(zs), int(n_paths), float(h), int(seed),
+                               int(tag), float(kappa), _ptr(phi), _ptr(xi), _ptr(steps),
+                               _ptr(iso), _ptr(xstop), _ptr(stats))
+    if rc != 0:
+        raise RuntimeError(f"or_estimate_nodes failed: {rc}")
+    st = stats.reshape(n, len(STAT_NAMES))
+    out = {name: st[:, j].copy() for j, name in enumerate(STAT_NAMES)}
+    if per_path:
+        out["phi"] = phi.reshape(n, n_paths)
+        out["xi"] = xi.reshape(n, n_paths)
+        out["steps"] = steps.reshape(n, n_paths)
+        out["iso"] = iso.reshape(n, n_paths)
+        out["x_stop"] = xstop.reshape(n, n_paths, 3)[:, :, :dim]
+    return out
+
+
+def sample_paths(kind: int, nodes: np.ndarray, node_idx, path_idx, h: float, seed: int = 1234,
+                 tag: int = 0, cv: int = CV_NONE, grad: np.ndarray | None = None,
+                 grid_n: int = 0, c0: float = GOBET_MENOZZI_C0, y_exp: bool = False,
+                 max_steps: int | None = None):
+    """Per-path (phi, xi, steps) for explicitly listed (node, path) pairs."""
+    lib = _load()
+    dim = problem_dim(kind)
+    nodes = np.asarray(nodes, dtype=np.float64).reshape(-1, dim)
+    node_idx = np.ascontiguousarray(node_idx, dtype=np.uint32)
+    path_idx = np.ascontiguousarray(path_idx, dtype=np.uint32)
+    sel = nodes[node_idx.astype(np.int64)]
+    xs = np.ascontiguousarray(sel[:, 0])
+    ys = np.ascontiguousarray(sel[:, 1])
+    zs = np.ascontiguousarray(sel[:, 2]) if dim == 3 else None
+    if max_steps is None:
+        max_steps = default_max_steps(h)
+    m = node_idx.size
+    phi, xi, steps = np.zeros(m), np.zeros(m), np.zeros(m, dtype=np.int64)
+    if grad is not None:
+        grad = np.ascontiguousarray(grad, dtype=np.float64)
+    lib.or_sample_paths(kind, c0, int(y_exp), int(max_steps), cv, grid_n, _ptr(grad), m,
+                        _ptr(xs), _ptr(ys), _ptr(zs), _ptr(node_idx), _ptr(path_idx), float(h),
+                        int(seed), int(tag), _ptr(phi), _ptr(xi), _ptr(steps))
+    return {"phi": phi, "xi": xi, "steps": steps}
+
+
+def node_stats(phi, xi, steps, kappa: float = 1.0) -> dict:
+    """Per-node statistics of one node's per-path arrays (two-pass FP64)."""
+    lib = _load()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    steps = np.ascontiguousarray(steps, dtype=np.int64)
+    n = phi.size
+    tr = np.zeros(n, dtype=np.int32)
+    iso = np.zeros(n)
+    st = np.zeros(len(STAT_NAMES))
+    lib.or_node_stats(n, _ptr(phi), _ptr(xi), _ptr(steps), _ptr(tr), _ptr(iso), float(kappa),
+                      _ptr(st))
+    return {name: st[j] for j, name in enumerate(STAT_NAMES)}
