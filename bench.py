@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the PDD Monte Carlo nodal stage on GB300.
+
+Workload (one "step"): the 2D interfacial problem with 256 nodes (2x2
+subdomains, 4 interfaces x 64 nodes), 10^5 Euler-Maruyama paths per node at
+dt = 1e-4 (Gobet-Menozzi exit test), run four times per step: the plain
+estimator and the pathwise control variate built from three synthetic
+previous iterates v = u + eps sin(3 pi x) sin(2 pi y) on a 129^2 grid,
+eps in {1e-1, 1e-2, 1e-3}.  Inputs are resident in HBM; L2 is flushed
+between timed steps.
+
+Prints one JSON line: value = path-steps/s of the whole step (device-resident
+inputs), e2e = the same metric through the C ABI with host buffers, the
+roofline of the dominant (control-variate) kernel, the FP64 CPU oracle timed
+on the host cores as cpu_baseline, nodes/s at a fixed RMSE for every mode,
+and the SM clocks sampled during the timed region.
+
+``--impl reference`` times the oracle (the only other implementation of the
+method) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("path-steps/s and interfacial nodes/s at fixed RMSE; controlled vs plain; "
+          "p50/p99")
+UNIT = "path-steps/s"
+N_PATHS = 100_000
+DT = 1e-4
+GRID_N = 129
+EPS = [1e-1, 1e-2, 1e-3]
+SEED = 1234
+TARGET_RMSE = 1e-3
+# Algorithmic thread-instructions per path-step (planning count of the
+# per-step work: Philox share, Box-Muller, coefficients, updates, exit test,
+# and for the control variate the bilinear gradient and xi update).
+ALGO_INSTR = {"plain": 110.0, "cv": 150.0}
+WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
+            "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
+            "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-nodes", type=int, default=64)
+    ap.add_argument("--cpu-paths", type=int, default=1000)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- CPU oracle --
+def _oracle_task(task):
+    """One (pass, node) of the oracle on the host (spawned worker)."""
+    import numpy as np
+    import oracle
+    from paper_1512_02818_gb300 import workloads as W
+    eps, node, n_paths, tag = task
+    grad, cv, gn = None, oracle.CV_NONE, 0
+    if eps is not None:
+        grad = oracle.build_gradient(2, W.control_grid(0, GRID_N, eps))
+        cv, gn = oracle.CV_GRID, GRID_N
+    r = oracle.estimate_nodes(0, np.asarray(node, dtype=np.float32)[None], n_paths, DT, seed=SEED,
+                              tag=tag, cv=cv, grad=grad, grid_n=gn, per_path=False)
+    return float(r["mean_steps"][0]) * n_paths
+
+
+def oracle_pool_time(tasks, cores):
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_task, tasks[:cores])  # warm the workers (imports, table builds)
+        t0 = time.perf_counter()
+        steps = pool.map(_oracle_task, tasks)
+        dt = time.perf_counter() - t0
+    return sum(steps), dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ clocks ----
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_id: str | None):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, power, reasons = [], [], [], set()
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ helpers ---
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def stream_tag(rank: int, pass_idx: int) -> int:
+    """Independent Philox streams per rank (replicas of the same workload)."""
+    return 16 * rank + pass_idx
+
+
+# ---------------------------------------------------------------- our arm -----
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    uuid = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (
+        str(uuid) if uuid is not None else str(local))
+
+    # CPU baseline pool first (spawned workers, rank 0 at N=1 only)
+    cpu_baseline = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nodes_all = W.workload_nodes("c1")
+        stride = max(1, len(nodes_all) // args.cpu_nodes)
+        sample = nodes_all[::stride][: args.cpu_nodes]
+        tasks = [(1e-2, tuple(map(float, x)), args.cpu_paths, 2) for x in sample]
+        cores = cpu_cores()
+        steps, secs = oracle_pool_time(tasks, cores)
+        cpu_baseline = {"value": steps / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": (f"{len(tasks)} nodes x {args.cpu_paths} paths of the eps=1e-2 "
+                                   f"control-variate pass ({steps:.3g} path-steps, "
+                                   f"{secs:.1f} s wall, FP64, one process per core)")}
+
+    ctx = pdd.Context(local)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    for slot, eps in enumerate(EPS):
+        prob.set_control_grid(slot, W.control_grid(0, GRID_N, eps))
+    nodes_np = W.workload_nodes("c1")
+    n_nodes = nodes_np.shape[0]
+    cols_dev = [torch.from_numpy(np.ascontiguousarray(nodes_np[:, j])).to(dev) for j in range(2)]
+    cols_host = [torch.from_numpy(np.ascontiguousarray(nodes_np[:, j])).pin_memory()
+                 for j in range(2)]
+    passes = [("plain", pdd.PDD_CV_NONE)] + [(f"eps{e:g}", i) for i, e in enumerate(EPS)]
+
+    def step(host=False):
+        out = []
+        for pi, (_, gid) in enumerate(passes):
+            out.append(prob.estimate(cols_host if host else cols_dev, N_PATHS, DT, grid_id=gid,
+                                     seed=SEED, stream_tag=stream_tag(rank, pi),
+                                     async_=not host, device_out=not host, host_inputs=host,
+                                     pin_host=host))
+        return out
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.kernel_time()  # drop warm-up events
+    launches0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_id)
+    results = None
+    for s in range(args.steps):
+        flush.zero_()  # L2 flush (256 MB > 126 MB L2), outside the timed events
+        ev[s][0].record()
+        results = step()
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    launches = ctx.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    _, n_timed, per_launch = ctx.kernel_time()
+    ctx.set_timing(False)
+
+    # work of one step, from the results (deterministic, identical every step)
+    res_np = [{k: v.cpu().numpy() for k, v in r.items() if torch.is_tensor(v)} for r in results]
+    pass_steps = [float((r["mean_steps"] * r["n_paths"]).sum()) for r in res_np]
+    steps_per_step = sum(pass_steps)
+    total_ms = max(1e-9, sum(step_ms))
+    total_ms_max = reduce_max(total_ms, world)
+    total_work = reduce_sum(steps_per_step * args.steps, world)
+    value = total_work / (total_ms_max / 1e3)
+
+    # per-pass kernel durations (launch order: plain, eps1, eps2, eps3 per step)
+    P = len(passes)
+    dur = {name: [per_launch[s * P + i] for s in range(args.steps)]
+           for i, (name, _) in enumerate(passes)}
+    rate = {name: pass_steps[i] / (statistics.mean(dur[name]) / 1e3)
+            for i, (name, _) in enumerate(passes)}
+    kappa = {name: rate["plain"] / rate[name] for name, _ in passes[1:]}
+
+    # roofline of the dominant kernel: the control-variate path kernel (eps 1e-2)
+    dom = "eps0.01"
+    avg_ms = statistics.mean(dur[dom])
+    instr = ALGO_INSTR["cv"] * pass_steps[2]
+    achieved = instr / (avg_ms / 1e3) / 1e12
+    peak = sms * 4 * 32 * 2.070e9 / 1e12  # one warp instruction per SMSP per cycle at max clock
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T thread-instr/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "paths_2d<Cfg0,float,grid-CV>",
+                "algorithmic": f"{ALGO_INSTR['cv']:.0f} thread-instr per path-step x "
+                               f"{pass_steps[2]:.4g} path-steps per launch",
+                "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x 2070 MHz"}
+
+    # nodes/s at a fixed RMSE (balanced choice of N per node, Sec. 3.1)
+    u = W.exact_u(0, nodes_np.astype(np.float64))
+    fixed = {}
+    for i, (name, _) in enumerate(passes):
+        r = res_np[i]
+        var = r["var_phi"] if name == "plain" else r["var_cv"]
+        mean = r["mean_phi"] if name == "plain" else r["mean_cv"]
+        need = np.ceil(var / (TARGET_RMSE**2 / 2.0))
+        secs = float((need * r["mean_steps"]).sum()) / rate[name]
+        fixed[name] = {"nodes_per_s": n_nodes / secs,
+                       "rmse_at_1e5_paths": float(np.sqrt(np.mean((mean - u) ** 2))),
+                       "median_var": float(np.median(var))}
+    for i, (name, _) in enumerate(passes):
+        if i == 0:
+            continue
+        r = res_np[i]
+        fixed[name]["speedup_vs_plain"] = fixed[name]["nodes_per_s"] / fixed["plain"]["nodes_per_s"]
+        pred = r["var_phi"] / (kappa[name] * r["var_cv"])
+        fixed[name]["predicted_speedup_median"] = float(np.median(pred))
+        fixed[name]["kappa"] = kappa[name]
+
+    # end to end through the C ABI with host buffers (pinned), copies included
+    torch.cuda.synchronize()
+    e2e_s = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(host=True)
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = reduce_max(sum(e2e_s), world)
+    e2e_value = reduce_sum(steps_per_step * len(e2e_s), world) / e2e_total
+    h2d = len(passes) * 2 * n_nodes * 4
+    d2h = len(passes) * (len(pdd.STAT_FIELDS) + len(pdd.COUNT_FIELDS)) * n_nodes * 8
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_nodes": n_nodes, "n_paths": N_PATHS, "dt": DT,
+                   "grid": GRID_N, "eps": EPS, "passes_per_step": len(passes),
+                   "path_steps_per_step": steps_per_step, "l2": "flushed between steps (256 MB)",
+                   "parallelism": f"replicas x{world} (independent Philox streams per rank)"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "cpu_baseline": cpu_baseline,
+        "fixed_rmse": {"target_rmse": TARGET_RMSE, **fixed},
+        "pass_rate_path_steps_per_s": rate,
+        "clocks": clk,
+        "timed_kernel_launches": n_timed,
+    }
+    prob.close()
+    ctx.close()
+    return line
+
+
+# ---------------------------------------------------------- reference arm -----
+def run_reference(args):
+    import numpy as np
+    from paper_1512_02818_gb300 import workloads as W
+    nodes_all = W.workload_nodes("c1")
+    sample = nodes_all[::8][:32]
+    paths = 400
+    eps_list = [None] + EPS
+    tasks = [(e, tuple(map(float, x)), paths, pi) for pi, e in enumerate(eps_list)
+             for x in sample]
+    cores = cpu_cores()
+    for _ in range(args.warmup):
+        pass  # the pool warm-up inside oracle_pool_time covers imports
+    times, work = [], []
+    for _ in range(args.steps):
+        steps, secs = oracle_pool_time(tasks, cores)
+        times.append(secs)
+        work.append(steps)
+    value = sum(work) / sum(times)
+    sample_desc = (f"{len(sample)} of 256 nodes x {paths} paths x 4 passes per step "
+                   f"(plain + 3 control-variate grids), FP64, one process per core")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_nodes": 256, "n_paths": N_PATHS, "dt": DT,
+                   "grid": GRID_N, "eps": EPS, "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

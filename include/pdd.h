@@ -1,0 +1,214 @@
+/*
+ * pdd.h -- C ABI of libpdd.so: the Monte Carlo nodal stage of Probabilistic
+ * Domain Decomposition (Bernal & Acebron, "A multigrid-like algorithm for
+ * probabilistic domain decomposition"), on one NVIDIA GB300 (sm_103a).
+ *
+ * For each interfacial node x0 the library simulates many Euler-Maruyama
+ * paths of dX = b dt + sigma dW (Sec. 2.1, eq. F:SDE) until the first exit
+ * from the unit box [0,1]^D, with the Gobet-Menozzi shrunken-boundary test or
+ * the naive test (Algorithm 1).  Along each path it accumulates the
+ * Feynman-Kac weights of eq. F:Dynkin / eq. F:VR_Milstein_sys,
+ *     Y_{k+1} = Y_k (1 - h c(X_k))       (or Y_k exp(-h c(X_k))),
+ *     Z_{k+1} = Z_k - h Y_k f(X_k),
+ * and the pathwise control variate of eq. F:xiControlVariate,
+ *     xi_{k+1} = xi_k - Y_k (sigma^T grad v(X_k)) . dW_k,
+ * where v is a previous, more accurate iterate given on a control grid
+ * (Sec. 3.1: "a D-dimensional array holding pointwise values").  The scores
+ * are phi = g(Pi X_tau) Y_tau + Z_tau and the controlled score phi + xi
+ * (eqs. F:Statistics_VR, F:Combining_method).  Per node it returns sample
+ * means, variances (N - 1), the covariance and Pearson correlation of
+ * (phi, xi) (eq. F:Rho), standard errors sqrt(V/N) (eq. F:Statistical_error),
+ * the variance ratio V[phi+xi]/V[phi] (eq. F:Variance_Reduction) and the
+ * predicted speedup V[phi] / (kappa V[phi+xi]) from the nodal cost model
+ * (eqs. F:Pointwise_cost and F:VR_Pointwise_cost), and the mean number of
+ * steps nu = E[tau]/h (eq. F:nu).
+ *
+ * PDE sign convention: 1/2 sum_ij a_ij d_ij u + b . grad u - c u = f with
+ * c >= 0 (the paper writes +c with c <= 0).
+ *
+ * Conventions of every call:
+ *   - Every function returns a pdd_status (or void for destructors).  No call
+ *     aborts, throws or exits; on a non-OK status pdd_last_error() returns a
+ *     message (thread-local, valid until the next call on the same thread).
+ *   - The library owns the opaque handles and all device memory it allocates.
+ *     The caller owns every input and output buffer; the library never frees
+ *     or retains them beyond the call (or, with PDD_FLAG_ASYNC, beyond the
+ *     completion of the work enqueued on the context's stream).
+ *   - Results are deterministic functions of (problem, grid contents, node
+ *     coordinates, node index, n_paths, dt, seed, stream_tag): sums are kept
+ *     in exact fixed-point integer arithmetic, so the order in which the GPU
+ *     finishes paths does not change a single bit.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (seed_lo32, stream_tag) and counter (block, path, node, seed_hi32);
+ *     normal number i of a path is Box-Muller output i % 4 of block i / 4;
+ *     step k uses normals D k .. D k + D - 1.
+ */
+#ifndef PDD_H
+#define PDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDD_ABI_VERSION 1
+
+typedef enum {
+  PDD_OK = 0,
+  PDD_ERR_INVALID = -1,   /* bad argument; nothing was enqueued */
+  PDD_ERR_NOMEM = -2,     /* device allocation failed or memory budget exceeded */
+  PDD_ERR_CUDA = -3,      /* a CUDA runtime call failed (message has the CUDA error) */
+  PDD_ERR_TIMEOUT = -4,   /* a bounded wait ran out */
+  PDD_ERR_BUSY = -5,      /* admission queue full / resource in use; retry later */
+  PDD_ERR_NOT_READY = -6, /* poll: request still running */
+  PDD_ERR_CANCELLED = -7, /* poll: request was cancelled */
+  PDD_ERR_OVERFLOW = -8,  /* a score left the fixed-point range |score| < 32768 */
+  PDD_WARN_TRUNCATED = 1  /* results valid, but some paths hit max_steps */
+} pdd_status;
+
+/* Built-in problems on the unit box [0,1]^D (the synthetic workloads).     */
+typedef enum {
+  /* D=2, b = (sin y / 2, cos x / 2), c = 1 + x^2 + y^2, sigma = I,
+     u = e^{x+y} cos(x-y), f from the PDE, g = u.                          */
+  PDD_PROBLEM_CFG0_2D = 0,
+  /* D=2, A = (1 + sin(2 pi x)/2) [[1, 1/2], [1/2, 1]], sigma its lower
+     Cholesky factor, b, c, u as CFG0_2D, f from the PDE.                  */
+  PDD_PROBLEM_ANISO_2D = 1,
+  /* D=3, b = 0, c = 1, sigma = I, u = e^x sin y cos z + x y z.            */
+  PDD_PROBLEM_CUBE_3D = 2,
+  /* D=2, b = c = f = 0, sigma = I, g = u = x^2 - y^2 (harmonic).          */
+  PDD_PROBLEM_HARMONIC_2D = 3
+} pdd_problem_kind;
+
+typedef enum {
+  PDD_EXIT_GOBET_MENOZZI = 0, /* finish when d(X_k) >= -0.5826 |sigma^T N| sqrt(h) (Algorithm 1) */
+  PDD_EXIT_NAIVE = 1          /* finish when d(X_k) >= 0 (weak order 1/2, Sec. 2.3) */
+} pdd_exit_rule;
+
+typedef enum {
+  PDD_Y_EULER = 0, /* Y_{k+1} = Y_k (1 - h c_k), as in Algorithm 1 */
+  PDD_Y_EXP = 1    /* Y_{k+1} = Y_k exp(-h c_k) */
+} pdd_y_rule;
+
+typedef enum {
+  PDD_PATH_FP32 = 0, /* path arithmetic in FP32 (compensated Z and xi sums) */
+  PDD_PATH_FP64 = 1  /* path arithmetic in FP64 */
+} pdd_path_precision;
+
+typedef enum { PDD_GRID_VALUES = 0, PDD_GRID_GRADIENT = 1 } pdd_grid_kind;
+typedef enum { PDD_DTYPE_F32 = 0, PDD_DTYPE_F64 = 1 } pdd_dtype;
+
+#define PDD_CV_NONE (-1)     /* plain estimator only (xi = 0) */
+#define PDD_CV_EXACT (-2)    /* control variate from the analytic grad u (the "exact" CV) */
+#define PDD_MAX_GRIDS 8      /* control-grid slots per problem */
+#define PDD_FLAG_EMIT_PATHS 1u /* also write per-path phi, xi, steps */
+#define PDD_FLAG_ASYNC 2u      /* device inputs/outputs only: return once enqueued */
+
+typedef struct pdd_ctx pdd_ctx;
+typedef struct pdd_problem pdd_problem;
+typedef struct pdd_server pdd_server;
+
+typedef struct {
+  int32_t kind;      /* pdd_problem_kind */
+  int32_t exit_rule; /* pdd_exit_rule */
+  int32_t y_rule;    /* pdd_y_rule */
+  int32_t precision; /* pdd_path_precision */
+  int64_t max_steps; /* per-path cap; <= 0 means ceil(100 / dt) per estimate */
+} pdd_problem_desc;
+
+/* A control grid: n points per axis on [0,1]^D, spacing 1/(n-1), x index
+   fastest.  VALUES: n^D samples of v (the library takes centred differences
+   inside and second-order one-sided differences on the edges, in FP64, and
+   stores the gradient in FP32).  GRADIENT: n^D * D interleaved components.   */
+typedef struct {
+  int32_t n;         /* points per axis, 3 <= n <= 4097 (2D) / 513 (3D) */
+  int32_t kind;      /* pdd_grid_kind */
+  int32_t dtype;     /* pdd_dtype */
+  int32_t on_device; /* data is a device pointer */
+  const void* data;
+} pdd_grid_desc;
+
+typedef struct {
+  int64_t n_nodes;          /* 0 <= n_nodes < 2^32 (0: nothing to do) */
+  const float* coords[3];   /* SoA node coordinates x[], y[], z[] (D used) */
+  int32_t coords_on_device; /* coords are device pointers */
+  int32_t grid_id;          /* PDD_CV_NONE, PDD_CV_EXACT, or a grid slot */
+  int64_t n_paths;          /* paths per node, 1 <= n_paths < 2^32 */
+  double dt;                /* time step h > 0 */
+  double kappa;             /* per-step cost ratio CV/plain for pred_speedup; <= 0: 1 */
+  uint64_t seed;
+  uint32_t stream_tag;      /* Philox key word 1 (cascade level or request tag) */
+  uint32_t flags;           /* PDD_FLAG_* */
+  float* path_phi;          /* EMIT_PATHS: device, n_nodes * n_paths, node-major */
+  float* path_xi;           /* EMIT_PATHS: device, same layout */
+  int32_t* path_steps;      /* EMIT_PATHS: device, same layout */
+} pdd_estimate_args;
+
+/* Caller-owned per-node outputs (SoA, n_nodes entries each).  Any pointer may
+   be NULL (not written).  on_device selects device or host pointers.        */
+typedef struct {
+  int32_t on_device;
+  int32_t reserved;
+  double* mean_phi;     /* E[phi] estimate */
+  double* var_phi;      /* V[phi] (N - 1) */
+  double* mean_cv;      /* E[phi + xi] */
+  double* var_cv;       /* V[phi + xi] */
+  double* cov_phi_xi;   /* Cov[phi, xi] */
+  double* var_xi;       /* V[xi] */
+  double* rho;          /* Pearson rho[phi, xi]; NaN without a control variate */
+  double* se_phi;       /* sqrt(V[phi] / N) */
+  double* se_cv;        /* sqrt(V[phi + xi] / N) */
+  double* vr;           /* V[phi + xi] / V[phi] */
+  double* pred_speedup; /* V[phi] / (kappa V[phi + xi]) */
+  double* mean_steps;   /* E[tau_h] / h */
+  uint64_t* n_paths;    /* paths accumulated */
+  uint64_t* n_truncated;/* paths stopped by max_steps */
+} pdd_node_stats;
+
+/* Library ABI version (PDD_ABI_VERSION of the build). */
+int pdd_abi_version(void);
+
+/* Thread-local message for the last non-OK status returned on this thread. */
+const char* pdd_last_error(void);
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+   enqueue on (e.g. torch.cuda.current_stream().cuda_stream), or NULL for a
+   stream the context creates and owns.  mem_budget: cap in bytes on the
+   context's workspace (0 = no cap).  *out receives the handle.              */
+int pdd_ctx_create(int device, void* cuda_stream, size_t mem_budget, pdd_ctx** out);
+void pdd_ctx_destroy(pdd_ctx* ctx);
+/* Switch the stream; waits for the previous stream's pending work first. */
+int pdd_ctx_set_stream(pdd_ctx* ctx, void* cuda_stream);
+/* Kernel timing: when enabled, every path-kernel launch is bracketed by CUDA
+   events on the launching stream.  pdd_ctx_kernel_time waits for them and
+   returns the summed milliseconds and the number of timed launches since the
+   previous call; per_launch_ms (nullable, `capacity` entries) receives the
+   individual durations in launch order.  The event list is then cleared.   */
+int pdd_ctx_set_timing(pdd_ctx* ctx, int enable);
+int pdd_ctx_kernel_time(pdd_ctx* ctx, double* total_ms, int64_t* launches, double* per_launch_ms,
+                        int64_t capacity);
+/* Number of library kernels launched by this context since creation. */
+int pdd_ctx_launch_count(pdd_ctx* ctx, int64_t* launches);
+
+int pdd_create_problem(pdd_ctx* ctx, const pdd_problem_desc* desc, pdd_problem** out);
+int pdd_destroy_problem(pdd_problem* problem);
+
+/* Copy a control grid into slot grid_id (0 <= grid_id < PDD_MAX_GRIDS) and
+   build its FP32 gradient table on the device (Sec. 3.1 lookup table; the
+   gradient that enters F = -sigma^T grad v, eq. F:ExactF).  The caller may
+   free `data` on return.  Waits for the context's stream before replacing
+   an existing grid.                                                         */
+int pdd_set_control_grid(pdd_problem* problem, int grid_id, const pdd_grid_desc* desc);
+
+/* Estimate all nodes: n_nodes x n_paths paths of Algorithm 1.  Synchronous
+   unless PDD_FLAG_ASYNC (allowed only with device coords and device outputs).
+   Returns PDD_WARN_TRUNCATED (synchronous calls) when any path hit
+   max_steps, PDD_ERR_OVERFLOW when a score left |score| < 32768.          */
+int pdd_estimate_nodes(pdd_problem* problem, const pdd_estimate_args* args, pdd_node_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDD_H */

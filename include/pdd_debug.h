@@ -1,0 +1,34 @@
+/*
+ * pdd_debug.h -- test hooks of libpdd.so.  They expose the device random
+ * number stages on their own so that tests can compare them with the oracle
+ * and with cuRAND's Philox4_32_10 generator; they are not part of the
+ * estimation path.  All pointers are device pointers; calls are synchronous;
+ * return a pdd_status (see pdd.h).
+ */
+#ifndef PDD_DEBUG_H
+#define PDD_DEBUG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Philox4x32-10 blocks: ctr[4*i..4*i+3], key[2*i..2*i+1] -> out[4*i..4*i+3]
+   (Salmon et al., SC'11), computed by the library's device generator.       */
+int pdd_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
+
+/* The same blocks from cuRAND's device API (curand_init(seed, subsequence,
+   offset) + curand4), as an independent implementation: seed = key0 |
+   key1 << 32, subsequence = ctr2 | ctr3 << 32, offset = 4 (ctr0 | ctr1 << 32). */
+int pdd_debug_philox_curand(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
+
+/* Normals first .. first+count-1 of the stream of (seed, tag, node, path), in
+   the path precision (precision 0: FP32 into out_f32; 1: FP64 into out_f64). */
+int pdd_debug_normals(uint64_t seed, uint32_t tag, uint32_t node, uint32_t path, uint64_t first,
+                      int64_t count, int precision, float* out_f32, double* out_f64);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PDD_DEBUG_H */

@@ -1,0 +1,368 @@
+// pdd_device.cuh -- device building blocks of the PDD Monte Carlo nodal stage:
+// the counter-based generator, the normal transform, the built-in problems,
+// the box geometry, the control-grid interpolation and the exact fixed-point
+// per-node accumulators.  Method: Bernal & Acebron, Sec. 2 and Algorithm 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdd_internal.h"
+
+namespace pdd {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Each of the ten rounds
+// multiplies words 0 and 2 by the two round multipliers, swaps the halves and
+// xors in the round key; the key is then bumped by the two Weyl increments.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Math in the path precision.  FP32 uses the SFU approximations (their error
+// is far below the Monte Carlo tolerance); FP64 uses the IEEE library calls.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float m_sin(float x) { return __sinf(x); }
+__device__ __forceinline__ float m_cos(float x) { return __cosf(x); }
+__device__ __forceinline__ float m_exp(float x) { return __expf(x); }
+__device__ __forceinline__ void m_sincos(float x, float* s, float* c) { __sincosf(x, s, c); }
+__device__ __forceinline__ float m_sqrt(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ double m_sin(double x) { return sin(x); }
+__device__ __forceinline__ double m_cos(double x) { return cos(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ void m_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+
+// Uniform (0,1) from a 32-bit word: ((w >> 9) + 1/2) 2^-23, exact in FP32.
+__device__ __forceinline__ float unit_f(uint32_t w) {
+  return fmaf((float)(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// Box-Muller pair from words (wa, wb): r = sqrt(-2 ln u_a), angle 2 pi u_b.
+// The angle is evaluated as theta = 2 pi (u_b - 1/2) in [-pi, pi] (where the
+// fast sine/cosine are accurate) and the signs flipped back:
+// cos(2 pi u) = -cos(theta), sin(2 pi u) = -sin(theta).
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
+  const float ua = unit_f(wa), ub = unit_f(wb);
+  const float t = -2.0f * __logf(ua);  // > 0 since ua < 1
+  const float r = t * rsqrtf(t);
+  const float th = fmaf(ub, 6.28318530717958647692f, -3.14159265358979323846f);
+  float s, c;
+  __sincosf(th, &s, &c);
+  n0 = -r * c;
+  n1 = -r * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
+  const double ua = ((double)(wa >> 9) + 0.5) * 0x1p-23;
+  const double ub = ((double)(wb >> 9) + 0.5) * 0x1p-23;
+  const double r = sqrt(-2.0 * log(ua));
+  const double th = (ub - 0.5) * 6.283185307179586476925286766559;
+  double s, c;
+  sincos(th, &s, &c);
+  n0 = -r * c;
+  n1 = -r * s;
+}
+
+// ---------------------------------------------------------------------------
+// Built-in problems (1/2 sum a_ij d_ij u + b.grad u - c u = f on [0,1]^D,
+// g = u).  eval() returns b, c, f at X_k and, when asked, the analytic grad u
+// used by the exact control variate.  sa = sqrt(a(x)) scales sigma for the
+// anisotropic problem, whose A = a(x) [[1, 1/2], [1/2, 1]] has equal diagonal
+// entries, so |sigma^T N| = sqrt(a) for either face normal.
+// ---------------------------------------------------------------------------
+template <class T>
+struct Coef {
+  T b0, b1, b2, c, f, g0, g1, g2, sa;
+};
+
+// u = e^{x+y} cos(x-y); Delta u = 0.
+template <class T, bool GRAD>
+__device__ __forceinline__ void exp_cos_2d(T x, T y, Coef<T>& o, T& u) {
+  const T sy = m_sin(y), cx = m_cos(x);
+  const T E = m_exp(x + y);
+  T sn, cs;
+  m_sincos(x - y, &sn, &cs);
+  u = E * cs;
+  const T ux = E * (cs - sn), uy = E * (cs + sn);
+  o.b0 = T(0.5) * sy;
+  o.b1 = T(0.5) * cx;
+  o.b2 = T(0);
+  o.c = T(1) + x * x + y * y;
+  o.f = o.b0 * ux + o.b1 * uy - o.c * u;
+  o.g0 = ux;
+  o.g1 = uy;
+  o.g2 = T(0);
+}
+
+struct Cfg0 {
+  static constexpr int kDim = 2;
+  static constexpr bool kAniso = false;
+  static constexpr bool kUnitY = false;
+  template <class T, bool GRAD>
+  __device__ __forceinline__ static void eval(T x, T y, T, Coef<T>& o) {
+    T u;
+    exp_cos_2d<T, GRAD>(x, y, o, u);
+    o.sa = T(1);
+  }
+  template <class T>
+  __device__ __forceinline__ static T g(T x, T y, T) {
+    return m_exp(x + y) * m_cos(x - y);
+  }
+  template <class T>
+  __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1); }
+};
+
+struct Aniso {
+  static constexpr int kDim = 2;
+  static constexpr bool kAniso = true;
+  static constexpr bool kUnitY = false;
+  // a(x) = 1 + sin(2 pi x)/2, with sin(2 pi x) = -sin(2 pi (x - 1/2)).
+  template <class T>
+  __device__ __forceinline__ static T a_of(T x) {
+    return T(1) - T(0.5) * m_sin(T(6.283185307179586476925286766559) * (x - T(0.5)));
+  }
+  template <class T, bool GRAD>
+  __device__ __forceinline__ static void eval(T x, T y, T, Coef<T>& o) {
+    T u;
+    exp_cos_2d<T, GRAD>(x, y, o, u);
+    const T a = a_of(x);
+    // 1/2 sum a_ij u_ij = 1/2 * 2 * (a/2) * u_xy with u_xy = 2u
+    o.f += a * u;
+    o.sa = m_sqrt(a);
+  }
+  template <class T>
+  __device__ __forceinline__ static T g(T x, T y, T) {
+    return m_exp(x + y) * m_cos(x - y);
+  }
+  template <class T>
+  __device__ __forceinline__ static T exit_scale(T x, T, T) { return m_sqrt(a_of(x)); }
+};
+
+struct Cube3 {
+  static constexpr int kDim = 3;
+  static constexpr bool kAniso = false;
+  static constexpr bool kUnitY = false;
+  template <class T, bool GRAD>
+  __device__ __forceinline__ static void eval(T x, T y, T z, Coef<T>& o) {
+    const T ex = m_exp(x);
+    T sy, cy, sz, cz;
+    if (GRAD) {
+      m_sincos(y, &sy, &cy);
+      m_sincos(z, &sz, &cz);
+    } else {
+      sy = m_sin(y);
+      cz = m_cos(z);
+      cy = sz = T(0);
+    }
+    const T e = ex * sy * cz;
+    o.b0 = o.b1 = o.b2 = T(0);
+    o.c = T(1);
+    // 1/2 Delta u - u with Delta u = -e^x sin y cos z
+    o.f = T(-1.5) * e - x * y * z;
+    o.g0 = e + y * z;
+    o.g1 = ex * cy * cz + x * z;
+    o.g2 = -ex * sy * sz + x * y;
+    o.sa = T(1);
+  }
+  template <class T>
+  __device__ __forceinline__ static T g(T x, T y, T z) {
+    return m_exp(x) * m_sin(y) * m_cos(z) + x * y * z;
+  }
+  template <class T>
+  __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1); }
+};
+
+struct Harmonic {
+  static constexpr int kDim = 2;
+  static constexpr bool kAniso = false;
+  static constexpr bool kUnitY = true;  // c = f = 0: Y = 1, Z = 0 on every path
+  template <class T, bool GRAD>
+  __device__ __forceinline__ static void eval(T x, T y, T, Coef<T>& o) {
+    o.b0 = o.b1 = o.b2 = T(0);
+    o.c = T(0);
+    o.f = T(0);
+    o.g0 = T(2) * x;
+    o.g1 = T(-2) * y;
+    o.g2 = T(0);
+    o.sa = T(1);
+  }
+  template <class T>
+  __device__ __forceinline__ static T g(T x, T y, T) { return x * x - y * y; }
+  template <class T>
+  __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1); }
+};
+
+// ---------------------------------------------------------------------------
+// Box geometry.  Inside [0,1]^D the exit test only needs the distance to the
+// nearest face, m = min_j min(x_j, 1 - x_j): d = -m, and outside the box m < 0
+// makes the finish condition hold as well.  The projection Pi clamps outside
+// points and moves the nearest coordinate onto its face inside (corner ties:
+// lowest axis first, the 0 face before the 1 face).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T face_distance(T x, T y) {
+  return fmin(fmin(x, T(1) - x), fmin(y, T(1) - y));
+}
+template <class T>
+__device__ __forceinline__ T face_distance(T x, T y, T z) {
+  return fmin(face_distance(x, y), fmin(z, T(1) - z));
+}
+
+template <class T>
+__device__ __forceinline__ void project_box(T* p, int dim) {
+  bool outside = false;
+  for (int j = 0; j < dim; ++j) outside |= (p[j] < T(0)) | (p[j] > T(1));
+  if (outside) {
+    for (int j = 0; j < dim; ++j) p[j] = fmin(fmax(p[j], T(0)), T(1));
+    return;
+  }
+  T best = p[0];
+  int sel = 0;
+  if (T(1) - p[0] < best) { best = T(1) - p[0]; sel = 1; }
+  for (int j = 1; j < dim; ++j) {
+    if (p[j] < best) { best = p[j]; sel = 2 * j; }
+    if (T(1) - p[j] < best) { best = T(1) - p[j]; sel = 2 * j + 1; }
+  }
+  p[sel >> 1] = (sel & 1) ? T(1) : T(0);
+}
+
+// ---------------------------------------------------------------------------
+// Control-grid interpolation: n points per axis on [0,1]^D, cell index
+// clamped to [0, n-2], multilinear weights.  2D tables are float2 (gx, gy),
+// 3D tables float4 (gx, gy, gz, 0) so every corner is one 8- or 16-byte load.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ int cell_of(T t, int n, T& frac) {
+  int i = (int)floor(t);
+  i = min(max(i, 0), n - 2);
+  frac = t - (T)i;
+  return i;
+}
+
+template <class T>
+__device__ __forceinline__ void grid_grad_2d(const float2* __restrict__ G, int n, T x, T y, T& gx,
+                                             T& gy) {
+  const T s = (T)(n - 1);
+  T fx, fy;
+  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy);
+  const float2* p = G + (size_t)iy * n + ix;
+  const float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + n), d = __ldg(p + n + 1);
+  const T lx0 = (T)a.x + fx * ((T)b.x - (T)a.x), lx1 = (T)c.x + fx * ((T)d.x - (T)c.x);
+  const T ly0 = (T)a.y + fx * ((T)b.y - (T)a.y), ly1 = (T)c.y + fx * ((T)d.y - (T)c.y);
+  gx = lx0 + fy * (lx1 - lx0);
+  gy = ly0 + fy * (ly1 - ly0);
+}
+
+template <class T>
+__device__ __forceinline__ void grid_grad_3d(const float4* __restrict__ G, int n, T x, T y, T z,
+                                             T& gx, T& gy, T& gz) {
+  const T s = (T)(n - 1);
+  T fx, fy, fz;
+  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy), iz = cell_of(z * s, n, fz);
+  const size_t nn = (size_t)n * n;
+  const float4* p = G + (size_t)iz * nn + (size_t)iy * n + ix;
+  T acc[3][2][2];  // [component][y corner][z corner] after the x lerp
+#pragma unroll
+  for (int cz = 0; cz < 2; ++cz) {
+#pragma unroll
+    for (int cy = 0; cy < 2; ++cy) {
+      const float4* q = p + cz * nn + cy * n;
+      const float4 a = __ldg(q), b = __ldg(q + 1);
+      acc[0][cy][cz] = (T)a.x + fx * ((T)b.x - (T)a.x);
+      acc[1][cy][cz] = (T)a.y + fx * ((T)b.y - (T)a.y);
+      acc[2][cy][cz] = (T)a.z + fx * ((T)b.z - (T)a.z);
+    }
+  }
+  T out[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T l0 = acc[c][0][0] + fy * (acc[c][1][0] - acc[c][0][0]);
+    const T l1 = acc[c][0][1] + fy * (acc[c][1][1] - acc[c][0][1]);
+    out[c] = l0 + fz * (l1 - l0);
+  }
+  gx = out[0];
+  gy = out[1];
+  gz = out[2];
+}
+
+// ---------------------------------------------------------------------------
+// Compensated (Kahan) summation for the FP32 Z and xi accumulators.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void kahan_add(T& sum, T& comp, T term) {
+  const T y = term - comp;
+  const T t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+// ---------------------------------------------------------------------------
+// Exact per-node accumulators.  Scores are converted to 64-bit fixed point
+// with 32 fractional bits (|score| < 2^15), products are formed exactly in
+// 128 bits, and 128-bit sums are kept in two 64-bit words with the carry of
+// the low word propagated by the adding thread.  Integer addition commutes, so
+// the totals do not depend on the order in which paths finish.
+// Layout of one node record (16 x u64):
+//   [0,1] sum q_phi   [2,3] sum q_phi^2   [4,5] sum q_psi   [6,7] sum q_psi^2
+//   [8,9] sum q_phi q_psi   [10,11] sum k   [12,13] sum k^2   [14] n   [15] n_trunc
+// (psi = phi + xi, the controlled score).
+// ---------------------------------------------------------------------------
+
+constexpr double kFxScale = 4294967296.0;  // 2^32
+constexpr double kFxLimit = 32768.0;       // |score| < 2^15
+
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* p, unsigned long long lo,
+                                                unsigned long long hi) {
+  const unsigned long long old = atomicAdd(p, lo);
+  hi += (old + lo < old) ? 1ull : 0ull;
+  if (hi != 0ull) atomicAdd(p + 1, hi);
+}
+
+__device__ __forceinline__ void atomic_add_s64(unsigned long long* p, long long v) {
+  atomic_add_u128(p, (unsigned long long)v, v < 0 ? ~0ull : 0ull);
+}
+
+__device__ __forceinline__ void atomic_add_prod(unsigned long long* p, long long a, long long b) {
+  atomic_add_u128(p, (unsigned long long)a * (unsigned long long)b,
+                  (unsigned long long)__mul64hi(a, b));
+}
+
+__device__ __forceinline__ bool to_fixed(double v, long long& q) {
+  if (!(fabs(v) < kFxLimit)) {
+    q = 0;
+    return false;
+  }
+  q = __double2ll_rn(v * kFxScale);
+  return true;
+}
+// FP32 scores: scaling by 2^32 is exact in FP32, so no FP64 work is needed.
+__device__ __forceinline__ bool to_fixed(float v, long long& q) {
+  if (!(fabsf(v) < (float)kFxLimit)) {
+    q = 0;
+    return false;
+  }
+  q = __float2ll_rn(v * 4294967296.0f);
+  return true;
+}
+
+// 128-bit two's-complement value (lo, hi) to double.
+__device__ __forceinline__ double s128_to_double(unsigned long long lo, unsigned long long hi) {
+  return (double)(long long)hi * 18446744073709551616.0 + (double)lo;
+}
+__device__ __forceinline__ double u128_to_double(unsigned long long lo, unsigned long long hi) {
+  return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+}  // namespace pdd

@@ -1,0 +1,80 @@
+// pdd_grid.cu -- control-grid preparation: the gradient lookup table of a
+// previous iterate v (the "D-dimensional array holding pointwise values" of
+// Sec. 3.1, entering the control variate F = -sigma^T grad v, eq. F:ExactF).
+// Centred differences inside, second-order one-sided differences on the
+// edges, in FP64; stored in FP32 as float2 (2D) or float4 (3D, w = 0).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pdd_internal.h"
+
+namespace pdd {
+
+__device__ __forceinline__ double diff_axis(const double* v, long long pt, long long i, long long n,
+                                            long long stride, double inv2d) {
+  if (i == 0) return (-3.0 * v[pt] + 4.0 * v[pt + stride] - v[pt + 2 * stride]) * inv2d;
+  if (i == n - 1) return (3.0 * v[pt] - 4.0 * v[pt - stride] + v[pt - 2 * stride]) * inv2d;
+  return (v[pt + stride] - v[pt - stride]) * inv2d;
+}
+
+__global__ void grid_gradient_kernel(const double* __restrict__ v, int n, int dim,
+                                     void* __restrict__ table) {
+  const long long nn = (long long)n;
+  const long long npts = (dim == 2) ? nn * nn : nn * nn * nn;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npts) return;
+  // 1 / (2 delta) with delta = 1 / (n - 1)
+  const double inv2d = 0.5 * (double)(n - 1);
+  const long long ix = pt % nn, iy = (pt / nn) % nn, iz = (dim == 3) ? pt / (nn * nn) : 0;
+  const double gx = diff_axis(v, pt, ix, nn, 1, inv2d);
+  const double gy = diff_axis(v, pt, iy, nn, nn, inv2d);
+  if (dim == 2) {
+    ((float2*)table)[pt] = make_float2((float)gx, (float)gy);
+  } else {
+    const double gz = diff_axis(v, pt, iz, nn, nn * nn, inv2d);
+    ((float4*)table)[pt] = make_float4((float)gx, (float)gy, (float)gz, 0.0f);
+  }
+}
+
+__global__ void grid_pack_kernel(const double* __restrict__ g, int n, int dim,
+                                 void* __restrict__ table) {
+  const long long nn = (long long)n;
+  const long long npts = (dim == 2) ? nn * nn : nn * nn * nn;
+  const long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pt >= npts) return;
+  if (dim == 2)
+    ((float2*)table)[pt] = make_float2((float)g[2 * pt], (float)g[2 * pt + 1]);
+  else
+    ((float4*)table)[pt] =
+        make_float4((float)g[3 * pt], (float)g[3 * pt + 1], (float)g[3 * pt + 2], 0.0f);
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ src, double* __restrict__ dst,
+                                  size_t count) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) dst[i] = (double)src[i];
+}
+
+static unsigned blocks_for(long long count, unsigned threads) {
+  return (unsigned)((count + threads - 1) / threads);
+}
+
+cudaError_t launch_grid_gradient(const double* v, int n, int dim, void* table, cudaStream_t st) {
+  const long long npts = (dim == 2) ? (long long)n * n : (long long)n * n * n;
+  grid_gradient_kernel<<<blocks_for(npts, 256), 256, 0, st>>>(v, n, dim, table);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_pack(const double* g, int n, int dim, void* table, cudaStream_t st) {
+  const long long npts = (dim == 2) ? (long long)n * n : (long long)n * n * n;
+  grid_pack_kernel<<<blocks_for(npts, 256), 256, 0, st>>>(g, n, dim, table);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float* src, double* dst, size_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  f32_to_f64_kernel<<<blocks_for((long long)count, 256), 256, 0, st>>>(src, dst, count);
+  return cudaGetLastError();
+}
+
+}  // namespace pdd

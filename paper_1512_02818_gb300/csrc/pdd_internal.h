@@ -1,0 +1,68 @@
+// pdd_internal.h -- structures shared by the host runtime and the kernels of
+// libpdd.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pdd {
+
+constexpr unsigned kErrOverflow = 1u;       // a score left the fixed-point range
+constexpr int kAccWords = 16;               // 64-bit words per node record
+constexpr unsigned long long kWarpBatch = 32;  // path indices a warp takes per cursor grab
+
+// Arguments of one path-kernel launch (passed by value as a grid constant).
+struct PathArgs {
+  const float* cx;
+  const float* cy;
+  const float* cz;
+  unsigned long long total;    // n_nodes * n_paths
+  unsigned long long n_paths;
+  unsigned long long* cursor;  // flat path cursor, zeroed before the launch
+  unsigned long long* acc;     // n_nodes x 16 words of exact sums, zeroed
+  unsigned* err;               // error bits (kErr*)
+  unsigned long long* trunc_total;
+  float* emit_phi;             // optional per-path outputs
+  float* emit_xi;
+  int* emit_steps;
+  const void* grad;            // float2 (2D) / float4 (3D) gradient table
+  int grid_n;
+  int max_steps;
+  int y_exp;
+  int max_blocks;              // 0 = occupancy x SM count
+  double h;
+  double sqrt_h;
+  double thr0;                 // c0 sqrt(h)
+  uint32_t key0, key1, seed_hi;
+};
+
+// Per-node output pointers (device; any may be null).
+struct StatPtrs {
+  double* mean_phi;
+  double* var_phi;
+  double* mean_cv;
+  double* var_cv;
+  double* cov_phi_xi;
+  double* var_xi;
+  double* rho;
+  double* se_phi;
+  double* se_cv;
+  double* vr;
+  double* pred_speedup;
+  double* mean_steps;
+  unsigned long long* n_paths;
+  unsigned long long* n_truncated;
+};
+
+cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int num_sms,
+                         cudaStream_t st, int* blocks);
+cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, double kappa,
+                            const StatPtrs& out, cudaStream_t st);
+// Gradient table of grid values v (FP64, n^D, x fastest) into float2/float4.
+cudaError_t launch_grid_gradient(const double* v, int n, int dim, void* table, cudaStream_t st);
+// Pack D interleaved gradient components (FP64) into float2/float4.
+cudaError_t launch_grid_pack(const double* g, int n, int dim, void* table, cudaStream_t st);
+// FP32 -> FP64 copy on the device.
+cudaError_t launch_f32_to_f64(const float* src, double* dst, size_t count, cudaStream_t st);
+
+}  // namespace pdd

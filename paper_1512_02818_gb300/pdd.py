@@ -1,0 +1,336 @@
+"""ctypes binding of libpdd.so (C ABI in include/pdd.h).
+
+The ``pdd_*`` functions below have the names and arguments of the C entry
+points; they only marshal arguments and turn non-OK statuses into
+``PddError``.  ``Context`` and ``Problem`` are small conveniences that take
+torch tensors (device memory and streams come from PyTorch) and return the
+per-node statistics as tensors.  Every step of the computation runs in the
+library's CUDA kernels; if the library is missing this module raises -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpdd.so")
+
+# ---- constants mirrored from include/pdd.h --------------------------------
+PDD_OK, PDD_ERR_INVALID, PDD_ERR_NOMEM, PDD_ERR_CUDA = 0, -1, -2, -3
+PDD_ERR_TIMEOUT, PDD_ERR_BUSY, PDD_ERR_NOT_READY, PDD_ERR_CANCELLED = -4, -5, -6, -7
+PDD_ERR_OVERFLOW, PDD_WARN_TRUNCATED = -8, 1
+PDD_PROBLEM_CFG0_2D, PDD_PROBLEM_ANISO_2D, PDD_PROBLEM_CUBE_3D, PDD_PROBLEM_HARMONIC_2D = 0, 1, 2, 3
+PDD_EXIT_GOBET_MENOZZI, PDD_EXIT_NAIVE = 0, 1
+PDD_Y_EULER, PDD_Y_EXP = 0, 1
+PDD_PATH_FP32, PDD_PATH_FP64 = 0, 1
+PDD_GRID_VALUES, PDD_GRID_GRADIENT = 0, 1
+PDD_DTYPE_F32, PDD_DTYPE_F64 = 0, 1
+PDD_CV_NONE, PDD_CV_EXACT = -1, -2
+PDD_MAX_GRIDS = 8
+PDD_FLAG_EMIT_PATHS, PDD_FLAG_ASYNC = 1, 2
+
+STAT_FIELDS = ["mean_phi", "var_phi", "mean_cv", "var_cv", "cov_phi_xi", "var_xi", "rho",
+               "se_phi", "se_cv", "vr", "pred_speedup", "mean_steps"]
+COUNT_FIELDS = ["n_paths", "n_truncated"]
+
+
+class PddError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"pdd status {status}: {message}")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("exit_rule", ctypes.c_int32),
+                ("y_rule", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("max_steps", ctypes.c_int64)]
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("kind", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("on_device", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class EstimateArgs(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("coords", ctypes.c_void_p * 3),
+                ("coords_on_device", ctypes.c_int32), ("grid_id", ctypes.c_int32),
+                ("n_paths", ctypes.c_int64), ("dt", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("stream_tag", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("path_phi", ctypes.c_void_p),
+                ("path_xi", ctypes.c_void_p), ("path_steps", ctypes.c_void_p)]
+
+
+class NodeStats(ctypes.Structure):
+    _fields_ = ([("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                + [(f, ctypes.c_void_p) for f in STAT_FIELDS + COUNT_FIELDS])
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("pdd_abi_version", ctypes.c_int, []),
+    ("pdd_last_error", ctypes.c_char_p, []),
+    ("pdd_ctx_create", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    ("pdd_ctx_destroy", None, [ctypes.c_void_p]),
+    ("pdd_ctx_set_stream", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("pdd_ctx_set_timing", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("pdd_ctx_kernel_time", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
+    ("pdd_ctx_launch_count", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    ("pdd_create_problem", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProblemDesc),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    ("pdd_destroy_problem", ctypes.c_int, [ctypes.c_void_p]),
+    ("pdd_set_control_grid", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.POINTER(GridDesc)]),
+    ("pdd_estimate_nodes", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
+                                          ctypes.POINTER(NodeStats)]),
+    ("pdd_debug_philox", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int64]),
+    ("pdd_debug_philox_curand", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int64]),
+    ("pdd_debug_normals", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                         ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
+                                         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+]
+
+
+def lib():
+    """Load libpdd.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+            l = ctypes.CDLL(LIB_PATH)
+            for name, res, args in _SIGS:
+                fn = getattr(l, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = l
+        return _lib
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        raise PddError(status, lib().pdd_last_error().decode(errors="replace"))
+    return status
+
+
+# ---- thin wrappers with the C names -----------------------------------------
+def pdd_abi_version() -> int:
+    return lib().pdd_abi_version()
+
+
+def pdd_last_error() -> str:
+    return lib().pdd_last_error().decode(errors="replace")
+
+
+def pdd_ctx_create(device: int, cuda_stream: int | None, mem_budget: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pdd_ctx_create(device, cuda_stream, mem_budget, ctypes.byref(h)))
+    return h.value
+
+
+def pdd_ctx_destroy(ctx: int) -> None:
+    lib().pdd_ctx_destroy(ctx)
+
+
+def pdd_ctx_set_stream(ctx: int, cuda_stream: int | None) -> None:
+    _check(lib().pdd_ctx_set_stream(ctx, cuda_stream))
+
+
+def pdd_ctx_set_timing(ctx: int, enable: bool) -> None:
+    _check(lib().pdd_ctx_set_timing(ctx, int(enable)))
+
+
+def pdd_ctx_kernel_time(ctx: int, capacity: int = 4096) -> tuple[float, int, list[float]]:
+    """(total ms, launches, per-launch ms) of the timed path-kernel launches."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    per = (ctypes.c_double * capacity)()
+    _check(lib().pdd_ctx_kernel_time(ctx, ctypes.byref(ms), ctypes.byref(n), per, capacity))
+    return ms.value, n.value, list(per[: min(n.value, capacity)])
+
+
+def pdd_ctx_launch_count(ctx: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().pdd_ctx_launch_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def pdd_create_problem(ctx: int, desc: ProblemDesc) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pdd_create_problem(ctx, ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def pdd_destroy_problem(problem: int) -> None:
+    _check(lib().pdd_destroy_problem(problem))
+
+
+def pdd_set_control_grid(problem: int, grid_id: int, desc: GridDesc) -> None:
+    _check(lib().pdd_set_control_grid(problem, grid_id, ctypes.byref(desc)))
+
+
+def pdd_estimate_nodes(problem: int, args: EstimateArgs, out: NodeStats) -> int:
+    """Returns PDD_OK or PDD_WARN_TRUNCATED; raises on errors."""
+    return _check(lib().pdd_estimate_nodes(problem, ctypes.byref(args), ctypes.byref(out)))
+
+
+def pdd_debug_philox(ctr_ptr: int, key_ptr: int, out_ptr: int, n: int) -> None:
+    _check(lib().pdd_debug_philox(ctr_ptr, key_ptr, out_ptr, n))
+
+
+def pdd_debug_philox_curand(ctr_ptr: int, key_ptr: int, out_ptr: int, n: int) -> None:
+    _check(lib().pdd_debug_philox_curand(ctr_ptr, key_ptr, out_ptr, n))
+
+
+def pdd_debug_normals(seed: int, tag: int, node: int, path: int, first: int, count: int,
+                      precision: int, out_f32: int | None, out_f64: int | None) -> None:
+    _check(lib().pdd_debug_normals(seed, tag, node, path, first, count, precision, out_f32,
+                                   out_f64))
+
+
+# ---- torch conveniences ------------------------------------------------------
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """A library context on one device, enqueuing on a torch stream."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0):
+        torch = _torch()
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.handle = pdd_ctx_create(device, self.stream.cuda_stream, mem_budget)
+
+    def set_stream(self, stream) -> None:
+        pdd_ctx_set_stream(self.handle, stream.cuda_stream)
+        self.stream = stream
+
+    def set_timing(self, enable: bool) -> None:
+        pdd_ctx_set_timing(self.handle, enable)
+
+    def kernel_time(self) -> tuple[float, int, list[float]]:
+        return pdd_ctx_kernel_time(self.handle)
+
+    def launch_count(self) -> int:
+        return pdd_ctx_launch_count(self.handle)
+
+    def close(self) -> None:
+        if self.handle:
+            pdd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Problem:
+    """A built-in problem with up to PDD_MAX_GRIDS control grids."""
+
+    def __init__(self, ctx: Context, kind: int, exit_rule: int = PDD_EXIT_GOBET_MENOZZI,
+                 y_rule: int = PDD_Y_EULER, precision: int = PDD_PATH_FP32, max_steps: int = 0):
+        self.ctx = ctx
+        self.kind = kind
+        self.dim = 3 if kind == PDD_PROBLEM_CUBE_3D else 2
+        self.precision = precision
+        self.handle = pdd_create_problem(ctx.handle, ProblemDesc(kind, exit_rule, y_rule,
+                                                                 precision, max_steps))
+
+    def set_control_grid(self, grid_id: int, data, kind: int = PDD_GRID_VALUES) -> None:
+        """data: numpy array or torch tensor (float32/float64, host or CUDA)
+        of shape (n,)*D (VALUES) or (n,)*D + (D,) (GRADIENT), x fastest."""
+        torch = _torch()
+        import numpy as np
+        if isinstance(data, np.ndarray):
+            data = torch.from_numpy(np.ascontiguousarray(data))
+        data = data.contiguous()
+        if data.dtype not in (torch.float32, torch.float64):
+            raise TypeError("grid data must be float32 or float64")
+        n = data.shape[0]
+        desc = GridDesc(n, kind, PDD_DTYPE_F32 if data.dtype == torch.float32 else PDD_DTYPE_F64,
+                        int(data.is_cuda), data.data_ptr())
+        pdd_set_control_grid(self.handle, grid_id, desc)
+
+    def estimate(self, nodes, n_paths: int, dt: float, grid_id: int = PDD_CV_NONE,
+                 seed: int = 1234, stream_tag: int = 0, kappa: float = 1.0,
+                 emit_paths: bool = False, device_out: bool = True, async_: bool = False,
+                 host_inputs: bool = False, pin_host: bool = False):
+        """Estimate every node.  nodes: (n, D) tensor or array of coordinates,
+        or a list of D contiguous float32 columns.  Returns a dict of per-node
+        tensors (and per-path tensors when emit_paths), plus 'status'.
+        host_inputs/device_out choose host or device buffers for the C call;
+        pin_host allocates host outputs in page-locked memory."""
+        torch = _torch()
+        import numpy as np
+        dev = torch.device("cuda", self.ctx.device)
+        if isinstance(nodes, (list, tuple)):
+            # pre-split SoA columns (float32, contiguous), used as given
+            cols = list(nodes)
+            n = cols[0].shape[0]
+            if any(c.is_cuda == host_inputs or c.dtype != torch.float32 for c in cols):
+                raise ValueError("columns must be float32 and on the side host_inputs says")
+        else:
+            if isinstance(nodes, np.ndarray):
+                nodes = torch.from_numpy(np.ascontiguousarray(nodes, dtype=np.float32))
+            nodes = nodes.to(torch.float32)
+            n = nodes.shape[0]
+            if host_inputs:
+                cols = [nodes[:, j].contiguous().cpu() for j in range(self.dim)]
+            else:
+                cols = [nodes[:, j].contiguous().to(dev) for j in range(self.dim)]
+        args = EstimateArgs()
+        args.n_nodes = n
+        for j in range(3):
+            args.coords[j] = cols[j].data_ptr() if j < self.dim else None
+        args.coords_on_device = 0 if host_inputs else 1
+        args.grid_id = grid_id
+        args.n_paths = n_paths
+        args.dt = dt
+        args.kappa = kappa
+        args.seed = seed
+        args.stream_tag = stream_tag
+        args.flags = (PDD_FLAG_EMIT_PATHS if emit_paths else 0) | (PDD_FLAG_ASYNC if async_ else 0)
+        res = {}
+        if emit_paths:
+            res["phi"] = torch.empty((n, n_paths), dtype=torch.float32, device=dev)
+            res["xi"] = torch.empty((n, n_paths), dtype=torch.float32, device=dev)
+            res["steps"] = torch.empty((n, n_paths), dtype=torch.int32, device=dev)
+            args.path_phi = res["phi"].data_ptr()
+            args.path_xi = res["xi"].data_ptr()
+            args.path_steps = res["steps"].data_ptr()
+        out = NodeStats()
+        out.on_device = 1 if device_out else 0
+        odev = dev if device_out else torch.device("cpu")
+        pin = (not device_out) and pin_host
+        for f in STAT_FIELDS:
+            res[f] = torch.empty(n, dtype=torch.float64, device=odev, pin_memory=pin)
+            setattr(out, f, res[f].data_ptr())
+        for f in COUNT_FIELDS:
+            res[f] = torch.empty(n, dtype=torch.int64, device=odev, pin_memory=pin)
+            setattr(out, f, res[f].data_ptr())
+        res["_keep"] = cols  # inputs must outlive an asynchronous call
+        res["status"] = pdd_estimate_nodes(self.handle, args, out)
+        return res
+
+    def close(self) -> None:
+        if self.handle:
+            pdd_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

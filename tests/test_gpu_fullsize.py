@@ -1,0 +1,61 @@
+"""Full-size checks in the launch configuration the benchmark times: the
+2D workload with 256 nodes x 10^5 paths at dt = 1e-4 and the eps = 1e-2
+control grid on 129^2 points.
+
+* sampled paths: the same launch with per-path output; a random sample of
+  (node, path) pairs is recomputed by the oracle one by one;
+* the per-node statistics of that launch equal, bit for bit, those of the
+  launch without per-path output (the configuration the benchmark times);
+* properties at full size: every node's controlled and plain means lie within
+  4 standard errors (plus an O(h) bias allowance) of the exact solution, and
+  the control variate reduces the variance.
+"""
+import numpy as np
+import pytest
+
+from paper_1512_02818_gb300 import workloads as W
+from parity import PATH_ATOL
+
+pytestmark = pytest.mark.gpu
+
+
+def test_c1_full_size_sampled_parity():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    from paper_1512_02818_gb300 import build, pdd
+    build.build()
+    oracle.build()
+    ctx = pdd.Context(0)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    v = W.control_grid(0, 129, 1e-2)
+    prob.set_control_grid(0, v)
+    nodes = W.workload_nodes("c1")
+    N, h = 100_000, 1e-4
+    full = prob.estimate(nodes, N, h, grid_id=0, seed=1234, stream_tag=2, emit_paths=True)
+    bench = prob.estimate(nodes, N, h, grid_id=0, seed=1234, stream_tag=2, async_=True)
+    torch.cuda.synchronize()
+    for f in pdd.STAT_FIELDS + pdd.COUNT_FIELDS:
+        assert np.array_equal(full[f].cpu().numpy(), bench[f].cpu().numpy(), equal_nan=True), f
+    rng = np.random.default_rng(5)
+    m = 400
+    ni = rng.integers(0, nodes.shape[0], size=m)
+    pi = rng.integers(0, N, size=m)
+    grad = oracle.build_gradient(2, v)
+    ref = oracle.sample_paths(0, nodes, ni, pi, h, seed=1234, tag=2, cv=oracle.CV_GRID,
+                              grad=grad, grid_n=129)
+    phi = full["phi"][torch.from_numpy(ni), torch.from_numpy(pi)].cpu().numpy()
+    xi = full["xi"][torch.from_numpy(ni), torch.from_numpy(pi)].cpu().numpy()
+    steps = full["steps"][torch.from_numpy(ni), torch.from_numpy(pi)].cpu().numpy()
+    same = steps == ref["steps"]
+    ok = same & (np.abs(phi - ref["phi"]) <= PATH_ATOL) & (np.abs(xi - ref["xi"]) <= PATH_ATOL)
+    assert ok.mean() >= 0.995, (ok.mean(), (~same).sum())
+    u = W.exact_u(0, nodes.astype(np.float64))
+    for mean, se in (("mean_cv", "se_cv"), ("mean_phi", "se_phi")):
+        err = np.abs(full[mean].cpu().numpy() - u)
+        assert np.all(err <= 4.5 * full[se].cpu().numpy() + 5e-4), (mean, err.max())
+    assert np.all(full["vr"].cpu().numpy() < 0.05)
+    assert np.all(full["n_truncated"].cpu().numpy() == 0)
+    prob.close()
+    ctx.close()
