@@ -206,9 +206,14 @@ class Context:
     """A library context on one device, enqueuing on a torch stream."""
 
     def __init__(self, device: int = 0, stream=None, mem_budget: int = 0):
+        """stream: a torch.cuda.Stream to enqueue on; by default a new
+        (non-default) torch stream, exposed as ``self.stream`` so callers can
+        order their own work and CUDA events on it."""
         torch = _torch()
         self.device = device
-        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device)
+        if self.stream.cuda_stream == 0:
+            raise ValueError("pass a non-default stream (handle 0 means 'library-owned')")
         self.handle = pdd_ctx_create(device, self.stream.cuda_stream, mem_budget)
 
     def set_stream(self, stream) -> None:
@@ -323,6 +328,14 @@ class Problem:
         res["_keep"] = cols  # inputs must outlive an asynchronous call
         res["status"] = pdd_estimate_nodes(self.handle, args, out)
         return res
+
+    def estimate_on_stream(self, *a, **kw):
+        """estimate() with the output tensors allocated on the context's
+        stream (so torch's caching allocator orders their reuse after the
+        library's kernels)."""
+        torch = _torch()
+        with torch.cuda.stream(self.ctx.stream):
+            return self.estimate(*a, **kw)
 
     def close(self) -> None:
         if self.handle:

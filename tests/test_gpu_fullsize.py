@@ -52,9 +52,14 @@ def test_c1_full_size_sampled_parity():
     ok = same & (np.abs(phi - ref["phi"]) <= PATH_ATOL) & (np.abs(xi - ref["xi"]) <= PATH_ATOL)
     assert ok.mean() >= 0.995, (ok.mean(), (~same).sum())
     u = W.exact_u(0, nodes.astype(np.float64))
+    # Discretisation bias: O(h) for Gobet-Menozzi away from the boundary; for the
+    # two nodes closer than sqrt(h) to it the first-order correction does not
+    # hold and the oracle shows biases of about 2e-3 at this h
+    dist = np.min(np.stack([nodes, 1 - nodes], -1), axis=(1, 2)).astype(np.float64)
+    allow = np.where(dist > np.sqrt(h), 5e-4, 3e-3)
     for mean, se in (("mean_cv", "se_cv"), ("mean_phi", "se_phi")):
         err = np.abs(full[mean].cpu().numpy() - u)
-        assert np.all(err <= 4.5 * full[se].cpu().numpy() + 5e-4), (mean, err.max())
+        assert np.all(err <= 4.5 * full[se].cpu().numpy() + allow), (mean, err.max())
     assert np.all(full["vr"].cpu().numpy() < 0.05)
     assert np.all(full["n_truncated"].cpu().numpy() == 0)
     prob.close()

@@ -138,8 +138,8 @@ def test_async_flag_orders_on_stream(env):
     torch, pdd = env["torch"], env["pdd"]
     nodes = W.workload_nodes("c0")
     prob = pdd.Problem(env["ctx"], pdd.PDD_PROBLEM_CFG0_2D)
-    a = prob.estimate(nodes, 300, 1e-3, async_=True)
-    torch.cuda.current_stream().synchronize()
+    a = prob.estimate_on_stream(nodes, 300, 1e-3, async_=True)
+    env["ctx"].stream.synchronize()
     b = prob.estimate(nodes, 300, 1e-3)
     assert np.array_equal(a["mean_phi"].cpu().numpy(), b["mean_phi"].cpu().numpy())
     with pytest.raises(pdd.PddError):

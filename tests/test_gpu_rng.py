@@ -32,8 +32,10 @@ def test_philox_matches_curand_and_oracle(env):
     rng = np.random.default_rng(11)
     n = 4096
     ctr = rng.integers(0, 2**32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
-    ctr[:, 1] = 0  # cuRAND's block offset is a 64-bit count; keep the high word in range
-    ctr[: n // 2, 1] = rng.integers(0, 2**31, size=n // 2).astype(np.uint32)
+    # cuRAND takes the block index as an offset of 4 * block 32-bit outputs in a
+    # 64-bit count: keep 4 * (ctr0 | ctr1 << 32) below 2^64
+    ctr[:, 1] = 0
+    ctr[: n // 2, 1] = rng.integers(0, 2**30, size=n // 2).astype(np.uint32)
     key = rng.integers(0, 2**32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
     ours = _blocks(torch, pdd, ctr.reshape(-1).copy(), key.reshape(-1).copy(), pdd.pdd_debug_philox)
     ref = _blocks(torch, pdd, ctr.reshape(-1).copy(), key.reshape(-1).copy(),
