@@ -47,6 +47,10 @@ TARGET_RMSE = 1e-3
 # per-step work: Philox share, Box-Muller, coefficients, updates, exit test,
 # and for the control variate the bilinear gradient and xi update).
 ALGO_INSTR = {"plain": 110.0, "cv": 150.0}
+# DRAM bytes (read + write) per launch of the dominant kernel from the ncu
+# capture summarised in profiles/paths_2d_cv_profiling_case.md; None whenever
+# the kernel has changed since that capture.
+NCU_TRAFFIC_BYTES = 273152
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
@@ -295,7 +299,7 @@ def run_ours(args, rank, world, local):
     achieved = instr / (avg_ms / 1e3) / 1e12
     peak = sms * 4 * 32 * 2.070e9 / 1e12  # one warp instruction per SMSP per cycle at max clock
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "T thread-instr/s", "frac": achieved / peak, "traffic": None,
+                "unit": "T thread-instr/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES,
                 "kernel": "paths_2d<Cfg0,float,grid-CV>",
                 "algorithmic": f"{ALGO_INSTR['cv']:.0f} thread-instr per path-step x "
                                f"{pass_steps[2]:.4g} path-steps per launch",
