@@ -208,6 +208,33 @@ int pdd_set_control_grid(pdd_problem* problem, int grid_id, const pdd_grid_desc*
    max_steps, PDD_ERR_OVERFLOW when a score left |score| < 32768.          */
 int pdd_estimate_nodes(pdd_problem* problem, const pdd_estimate_args* args, pdd_node_stats* out);
 
+/* ---- Allocation-free estimate (the paper has no counterpart) -------------
+   The same estimate as pdd_estimate_nodes, for callers that cannot let the
+   library allocate device memory: for example an application whose own pool
+   allocator has reserved the device memory, or a latency-critical loop that
+   must not pay for cudaMalloc/cudaFree and the device-wide synchronisation
+   they can cause.  Instead of the context's workspace, its scratch (path
+   cursor, error bits and the per-node exact sums) is one fixed device array
+   of 256 + 128 * PDD_NOALLOC_MAX_NODES bytes (about 512 KiB), which every GPU
+   that loads the library holds until the process exits.  The call performs
+   no cudaMalloc, cudaFree or other allocating call.
+   - n_nodes <= PDD_NOALLOC_MAX_NODES, else PDD_ERR_INVALID with a message.
+   - Coordinates, outputs and EMIT_PATHS buffers must be device pointers
+     (host buffers would need device staging memory).
+   - Control grids are loaded beforehand with pdd_set_control_grid (which
+     allocates, so it belongs to set-up).
+   - The first call on each device looks up and caches the array's device
+     address (cudaGetSymbolAddress); make that first call before any stream
+     capture.
+   - Every call uses the same array, which keeps the previous call's contents
+     (each call clears what must start at zero).  Calls that can overlap on
+     the GPU -- different streams or different contexts -- race on it and give
+     wrong results: serialise them.  Calls on one context are serialised.
+   Flags, statuses and outputs are those of pdd_estimate_nodes.             */
+#define PDD_NOALLOC_MAX_NODES 4096
+int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estimate_args* args,
+                               pdd_node_stats* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -98,6 +98,30 @@ struct WsHeader {
   unsigned long long trunc_total;
 };
 
+namespace pdd {
+// Read-only view of a problem and its context for other translation units of
+// the library (the allocation-free entry point).
+bool problem_view(pdd_problem* p, ProblemView* v) {
+  if (!p || !p->ctx || !v) return false;
+  v->device = p->ctx->device;
+  v->stream = p->ctx->stream;
+  v->num_sms = p->ctx->num_sms;
+  v->kind = p->desc.kind;
+  v->precision = p->desc.precision;
+  v->exit_rule = p->desc.exit_rule;
+  v->y_rule = p->desc.y_rule;
+  v->max_steps = p->desc.max_steps;
+  v->dim = p->dim;
+  for (int i = 0; i < PDD_MAX_GRIDS; ++i) {
+    v->grid_table[i] = p->grids[i].table;
+    v->grid_n[i] = p->grids[i].n;
+  }
+  v->mu = &p->ctx->mu;
+  v->launches = &p->ctx->launches;
+  return true;
+}
+}  // namespace pdd
+
 static int ensure_workspace(pdd_ctx* c, size_t bytes) {
   if (c->ws_size >= bytes) return PDD_OK;
   if (c->budget != 0 && bytes > c->budget) {

@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
+#include "../../include/pdd.h"
+
 namespace pdd {
 
 constexpr unsigned kErrOverflow = 1u;       // a score left the fixed-point range
@@ -53,6 +57,22 @@ struct StatPtrs {
   unsigned long long* n_paths;
   unsigned long long* n_truncated;
 };
+
+// What the allocation-free entry point needs to know about a problem.
+struct ProblemView {
+  int device;
+  cudaStream_t stream;
+  int num_sms;
+  int kind, precision, exit_rule, y_rule, dim;
+  int64_t max_steps;
+  const void* grid_table[8];
+  int grid_n[8];
+  std::mutex* mu;
+  int64_t* launches;
+};
+
+static_assert(PDD_MAX_GRIDS == 8, "ProblemView holds 8 grid slots");
+bool problem_view(pdd_problem* p, ProblemView* v);
 
 cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int num_sms,
                          cudaStream_t st, int* blocks);

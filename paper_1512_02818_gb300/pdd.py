@@ -90,6 +90,8 @@ _SIGS = [
                                             ctypes.POINTER(GridDesc)]),
     ("pdd_estimate_nodes", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
                                           ctypes.POINTER(NodeStats)]),
+    ("pdd_estimate_nodes_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
+                                                  ctypes.POINTER(NodeStats)]),
     ("pdd_debug_philox", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int64]),
     ("pdd_debug_philox_curand", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p,
@@ -180,6 +182,18 @@ def pdd_set_control_grid(problem: int, grid_id: int, desc: GridDesc) -> None:
 def pdd_estimate_nodes(problem: int, args: EstimateArgs, out: NodeStats) -> int:
     """Returns PDD_OK or PDD_WARN_TRUNCATED; raises on errors."""
     return _check(lib().pdd_estimate_nodes(problem, ctypes.byref(args), ctypes.byref(out)))
+
+
+PDD_NOALLOC_MAX_NODES = 4096
+
+
+def pdd_estimate_nodes_noalloc(problem: int, args: EstimateArgs, out: NodeStats) -> int:
+    """Allocation-free estimate for callers that cannot let the library
+    allocate device memory (device inputs and outputs only, at most
+    PDD_NOALLOC_MAX_NODES nodes; see include/pdd.h).  Returns PDD_OK or
+    PDD_WARN_TRUNCATED; raises on errors."""
+    return _check(lib().pdd_estimate_nodes_noalloc(problem, ctypes.byref(args),
+                                                   ctypes.byref(out)))
 
 
 def pdd_debug_philox(ctr_ptr: int, key_ptr: int, out_ptr: int, n: int) -> None:
