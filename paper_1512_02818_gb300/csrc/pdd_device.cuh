@@ -19,11 +19,11 @@ namespace pdd {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    // one 32x32 -> 64-bit multiply gives both halves of each product
+    const unsigned long long p0 = (unsigned long long)c.x * 0xD2511F53u;
+    const unsigned long long p1 = (unsigned long long)c.z * 0xCD9E8D57u;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k.x, (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ k.y, (uint32_t)p0);
     k.x += 0x9E3779B9u;
     k.y += 0xBB67AE85u;
   }
@@ -54,20 +54,23 @@ __device__ __forceinline__ float unit_f(uint32_t w) {
 // The angle is evaluated as theta = 2 pi (u_b - 1/2) in [-pi, pi] (where the
 // fast sine/cosine are accurate) and the signs flipped back:
 // cos(2 pi u) = -cos(theta), sin(2 pi u) = -sin(theta).
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1) {
+// `scale` multiplies both outputs (the kernels pass sqrt(h) to get dW directly).
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& n0, float& n1,
+                                           float scale = 1.0f) {
   const float ua = unit_f(wa), ub = unit_f(wb);
   const float t = -2.0f * __logf(ua);  // > 0 since ua < 1
-  const float r = t * rsqrtf(t);
+  const float r = (scale * t) * rsqrtf(t);
   const float th = fmaf(ub, 6.28318530717958647692f, -3.14159265358979323846f);
   float s, c;
   __sincosf(th, &s, &c);
   n0 = -r * c;
   n1 = -r * s;
 }
-__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1) {
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, double& n0, double& n1,
+                                           double scale = 1.0) {
   const double ua = ((double)(wa >> 9) + 0.5) * 0x1p-23;
   const double ub = ((double)(wb >> 9) + 0.5) * 0x1p-23;
-  const double r = sqrt(-2.0 * log(ua));
+  const double r = scale * sqrt(-2.0 * log(ua));
   const double th = (ub - 0.5) * 6.283185307179586476925286766559;
   double s, c;
   sincos(th, &s, &c);

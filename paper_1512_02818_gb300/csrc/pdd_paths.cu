@@ -25,6 +25,9 @@
 namespace pdd {
 
 constexpr int kBlockThreads = 256;
+#ifndef PDD_MIN_BLOCKS
+#define PDD_MIN_BLOCKS 1
+#endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 enum { kCvNone = 0, kCvGrid = 1, kCvExact = 2 };
 
@@ -41,8 +44,14 @@ struct PathState {
 template <class T, int D>
 __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long g,
                                            PathState<T>& s) {
-  s.node = (uint32_t)(g / a.n_paths);
-  s.path = (uint32_t)(g - (unsigned long long)s.node * a.n_paths);
+  if (a.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
+    const uint32_t gg = (uint32_t)g, np = (uint32_t)a.n_paths;
+    s.node = gg / np;
+    s.path = gg - s.node * np;
+  } else {
+    s.node = (uint32_t)(g / a.n_paths);
+    s.path = (uint32_t)(g - (unsigned long long)s.node * a.n_paths);
+  }
   s.x[0] = (T)__ldg(a.cx + s.node);
   s.x[1] = (T)__ldg(a.cy + s.node);
   s.x[2] = (D == 3) ? (T)__ldg(a.cz + s.node) : T(0);
@@ -63,12 +72,12 @@ __device__ __forceinline__ bool should_finish(const PathState<T>& s, T thr0) {
 // One Euler-Maruyama step (eq. F:E_M) with the Feynman-Kac weights and the
 // control variate, all right-hand sides at X_k.
 template <class P, class T, int D, int CV>
-__device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s, T h, T sqh,
-                                           const T* n) {
+__device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s, T h,
+                                           const T* dW) {
   Coef<T> o;
   P::template eval<T, CV == kCvExact>(s.x[0], s.x[1], s.x[2], o);
   T sdW[3];
-  const T dW0 = sqh * n[0], dW1 = sqh * n[1];
+  const T dW0 = dW[0], dW1 = dW[1];
   if (P::kAniso) {  // sigma = sqrt(a) [[1, 0], [1/2, sqrt(3)/2]]
     sdW[0] = o.sa * dW0;
     sdW[1] = o.sa * (T(0.5) * dW0 + T(0.86602540378443864676) * dW1);
@@ -76,7 +85,7 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s, T
     sdW[0] = dW0;
     sdW[1] = dW1;
   }
-  sdW[2] = (D == 3) ? sqh * n[2] : T(0);
+  sdW[2] = (D == 3) ? dW[2] : T(0);
   if (CV != kCvNone) {
     T gv[3] = {T(0), T(0), T(0)};
     if (CV == kCvGrid) {
@@ -172,7 +181,7 @@ __device__ __forceinline__ bool refill(const PathArgs& a, PathState<T>& s, bool&
 }
 
 template <class P, class T, int CV>
-__global__ void __launch_bounds__(kBlockThreads) paths_2d(const __grid_constant__ PathArgs a) {
+__global__ void __launch_bounds__(kBlockThreads, PDD_MIN_BLOCKS) paths_2d(const __grid_constant__ PathArgs a) {
   const T h = (T)a.h, sqh = (T)a.sqrt_h, thr0 = (T)a.thr0;
   const uint2 key = make_uint2(a.key0, a.key1);
   PathState<T> s;
@@ -189,17 +198,17 @@ __global__ void __launch_bounds__(kBlockThreads) paths_2d(const __grid_constant_
     if (active && !fin) {
       w = philox4x32_10(make_uint4((uint32_t)(s.k >> 1), s.path, s.node, a.seed_hi), key);
       T n[3];
-      box_muller(w.x, w.y, n[0], n[1]);
+      box_muller(w.x, w.y, n[0], n[1], sqh);
       n[2] = T(0);
-      euler_step<P, T, 2, CV>(a, s, h, sqh, n);
+      euler_step<P, T, 2, CV>(a, s, h, n);
       if (s.k >= a.max_steps) fin = trunc = true;
     }
     if (active && !fin) fin = should_finish<P, T, 2>(s, thr0);
     if (active && !fin) {
       T n[3];
-      box_muller(w.z, w.w, n[0], n[1]);
+      box_muller(w.z, w.w, n[0], n[1], sqh);
       n[2] = T(0);
-      euler_step<P, T, 2, CV>(a, s, h, sqh, n);
+      euler_step<P, T, 2, CV>(a, s, h, n);
       if (s.k >= a.max_steps) fin = trunc = true;
     }
     if (active && fin) {
@@ -214,7 +223,7 @@ __global__ void __launch_bounds__(kBlockThreads) paths_2d(const __grid_constant_
 //   step 0: a0 a1 a2   step 1: a3 b0 b1   step 2: b2 b3 c0   step 3: c1 c2 c3
 // Blocks are drawn only when the path is still running.
 template <class P, class T, int CV>
-__global__ void __launch_bounds__(kBlockThreads) paths_3d(const __grid_constant__ PathArgs a) {
+__global__ void __launch_bounds__(kBlockThreads, PDD_MIN_BLOCKS) paths_3d(const __grid_constant__ PathArgs a) {
   const T h = (T)a.h, sqh = (T)a.sqrt_h, thr0 = (T)a.thr0;
   const uint2 key = make_uint2(a.key0, a.key1);
   PathState<T> s;
@@ -234,10 +243,10 @@ __global__ void __launch_bounds__(kBlockThreads) paths_3d(const __grid_constant_
     if (active && !fin) {
       w = philox4x32_10(make_uint4(blk0, s.path, s.node, a.seed_hi), key);
       T n[3], n3;
-      box_muller(w.x, w.y, n[0], n[1]);
-      box_muller(w.z, w.w, n[2], n3);
+      box_muller(w.x, w.y, n[0], n[1], sqh);
+      box_muller(w.z, w.w, n[2], n3, sqh);
       carry0 = n3;
-      euler_step<P, T, 3, CV>(a, s, h, sqh, n);
+      euler_step<P, T, 3, CV>(a, s, h, n);
       if (s.k >= a.max_steps) fin = trunc = true;
     }
     // step 1
@@ -246,18 +255,18 @@ __global__ void __launch_bounds__(kBlockThreads) paths_3d(const __grid_constant_
       w = philox4x32_10(make_uint4(blk0 + 1u, s.path, s.node, a.seed_hi), key);
       T n[3];
       n[0] = carry0;
-      box_muller(w.x, w.y, n[1], n[2]);
-      euler_step<P, T, 3, CV>(a, s, h, sqh, n);
+      box_muller(w.x, w.y, n[1], n[2], sqh);
+      euler_step<P, T, 3, CV>(a, s, h, n);
       if (s.k >= a.max_steps) fin = trunc = true;
     }
     // step 2
     if (active && !fin) fin = should_finish<P, T, 3>(s, thr0);
     if (active && !fin) {
       T n[3];
-      box_muller(w.z, w.w, n[0], n[1]);
+      box_muller(w.z, w.w, n[0], n[1], sqh);
       w = philox4x32_10(make_uint4(blk0 + 2u, s.path, s.node, a.seed_hi), key);
-      box_muller(w.x, w.y, n[2], carry1);
-      euler_step<P, T, 3, CV>(a, s, h, sqh, n);
+      box_muller(w.x, w.y, n[2], carry1, sqh);
+      euler_step<P, T, 3, CV>(a, s, h, n);
       if (s.k >= a.max_steps) fin = trunc = true;
     }
     // step 3
@@ -265,8 +274,8 @@ __global__ void __launch_bounds__(kBlockThreads) paths_3d(const __grid_constant_
     if (active && !fin) {
       T n[3];
       n[0] = carry1;
-      box_muller(w.z, w.w, n[1], n[2]);
-      euler_step<P, T, 3, CV>(a, s, h, sqh, n);
+      box_muller(w.z, w.w, n[1], n[2], sqh);
+      euler_step<P, T, 3, CV>(a, s, h, n);
       if (s.k >= a.max_steps) fin = trunc = true;
     }
     if (active && fin) {
