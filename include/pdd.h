@@ -105,6 +105,9 @@ typedef enum { PDD_DTYPE_F32 = 0, PDD_DTYPE_F64 = 1 } pdd_dtype;
 #define PDD_MAX_GRIDS 8      /* control-grid slots per problem */
 #define PDD_FLAG_EMIT_PATHS 1u /* also write per-path phi, xi, steps */
 #define PDD_FLAG_ASYNC 2u      /* device inputs/outputs only: return once enqueued */
+#define PDD_FLAG_GRAPH 4u      /* pdd_estimate_levels: capture the launch sequence in a CUDA
+                                  graph and replay it while the arguments repeat */
+#define PDD_MAX_LEVELS 32      /* levels (or batches) per pdd_estimate_levels call */
 
 typedef struct pdd_ctx pdd_ctx;
 typedef struct pdd_problem pdd_problem;
@@ -191,6 +194,13 @@ int pdd_ctx_kernel_time(pdd_ctx* ctx, double* total_ms, int64_t* launches, doubl
                         int64_t capacity);
 /* Number of library kernels launched by this context since creation. */
 int pdd_ctx_launch_count(pdd_ctx* ctx, int64_t* launches);
+/* Number of CUDA graphs captured by PDD_FLAG_GRAPH calls on this context. */
+int pdd_ctx_graph_count(pdd_ctx* ctx, int64_t* captures);
+/* Launch shape of the path kernels: block_threads (multiple of 32 in
+   [32, 512]; 0 = 256) and a cap on the grid size (0 = occupancy x SM count).
+   The shape changes only the speed: the results are exact sums keyed by
+   (node, path), identical for every shape.                                  */
+int pdd_ctx_set_launch(pdd_ctx* ctx, int block_threads, int max_blocks);
 
 int pdd_create_problem(pdd_ctx* ctx, const pdd_problem_desc* desc, pdd_problem** out);
 int pdd_destroy_problem(pdd_problem* problem);
@@ -207,6 +217,30 @@ int pdd_set_control_grid(pdd_problem* problem, int grid_id, const pdd_grid_desc*
    Returns PDD_WARN_TRUNCATED (synchronous calls) when any path hit
    max_steps, PDD_ERR_OVERFLOW when a score left |score| < 32768.          */
 int pdd_estimate_nodes(pdd_problem* problem, const pdd_estimate_args* args, pdd_node_stats* out);
+
+/* Several levels -- e.g. the levels of the multigrid-like cascade (Sec. 1,
+   Algorithm 5), each with its own nodes, n_paths, dt, control grid, seed,
+   stream_tag and outputs -- in ONE persistent launch: the paths of all levels
+   form one work list, levels with the smallest dt (the longest paths) first,
+   so short paths fill the tail of long ones.  Results are bit-identical to one
+   pdd_estimate_nodes call per level.  levels[l].flags may hold
+   PDD_FLAG_EMIT_PATHS; `flags` (the call's) may hold PDD_FLAG_ASYNC and
+   PDD_FLAG_GRAPH (both need device coordinates and outputs).  With
+   PDD_FLAG_GRAPH the clear / path-kernel / finalise sequence is captured once
+   into a CUDA graph (kept by the context) and replayed by later calls with
+   identical arguments; different arguments re-capture.  Levels may mix
+   control grids with plain levels (grid_id = PDD_CV_NONE) but not with
+   PDD_CV_EXACT.  n_levels in [1, PDD_MAX_LEVELS]; outs[l] receives level l. */
+int pdd_estimate_levels(pdd_problem* problem, int n_levels, const pdd_estimate_args* levels,
+                        pdd_node_stats* outs, uint32_t flags);
+
+/* Autotuner: runs `sample` (device coordinates) under candidate launch shapes
+   (128/256/512 threads per block, full and half occupancy), times each with
+   CUDA events on the context's stream, and keeps the fastest as the context's
+   launch shape (pdd_ctx_set_launch).  Outputs (nullable): the chosen shape and
+   its time.  Results of later calls do not depend on the choice.            */
+int pdd_autotune(pdd_problem* problem, const pdd_estimate_args* sample, int* best_threads,
+                 int* best_max_blocks, double* best_ms);
 
 /* ---- Allocation-free estimate (the paper has no counterpart) -------------
    The same estimate as pdd_estimate_nodes, for callers that cannot let the

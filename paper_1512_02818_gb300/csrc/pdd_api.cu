@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -76,6 +77,11 @@ struct pdd_ctx {
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   int64_t launches = 0;
+  int block_threads = 0;  // launch shape (0: defaults), set by pdd_ctx_set_launch / pdd_autotune
+  int max_blocks = 0;
+  cudaGraphExec_t gexec = nullptr;  // cached graph of the last PDD_FLAG_GRAPH call
+  uint64_t gkey = 0;
+  int64_t graph_captures = 0;
 };
 
 struct GridSlot {
@@ -141,6 +147,373 @@ static int ensure_workspace(pdd_ctx* c, size_t bytes) {
   return PDD_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Estimation of one or several levels in one persistent launch.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct LevelPlan {
+  int cv;              // 0 none, 1 grid, 2 exact
+  const void* table;
+  int grid_n;
+  int64_t max_steps;
+};
+
+int check_level(const pdd_problem* p, const pdd_estimate_args* a, const pdd_node_stats* out,
+                const char* who, int l, LevelPlan* lp) {
+  const int dim = p->dim;
+  if (a->n_nodes < 0 || a->n_nodes >= (int64_t)1 << 32) {
+    set_error("%s: level %d: n_nodes = %lld outside [0, 2^32)", who, l, (long long)a->n_nodes);
+    return PDD_ERR_INVALID;
+  }
+  if (a->n_paths < 1 || a->n_paths >= (int64_t)1 << 32) {
+    set_error("%s: level %d: n_paths = %lld outside [1, 2^32)", who, l, (long long)a->n_paths);
+    return PDD_ERR_INVALID;
+  }
+  if (!(a->dt > 0.0) || !std::isfinite(a->dt)) {
+    set_error("%s: level %d: dt must be finite and > 0", who, l);
+    return PDD_ERR_INVALID;
+  }
+  if ((unsigned long long)a->n_nodes * (unsigned long long)a->n_paths >= (1ull << 62)) {
+    set_error("%s: level %d: n_nodes * n_paths too large", who, l);
+    return PDD_ERR_INVALID;
+  }
+  if (a->flags & ~(PDD_FLAG_EMIT_PATHS | PDD_FLAG_ASYNC)) {
+    set_error("%s: level %d: unknown flags 0x%x", who, l, a->flags);
+    return PDD_ERR_INVALID;
+  }
+  if ((a->flags & PDD_FLAG_EMIT_PATHS) && (!a->path_phi || !a->path_xi || !a->path_steps)) {
+    set_error("%s: level %d: EMIT_PATHS needs path_phi, path_xi and path_steps", who, l);
+    return PDD_ERR_INVALID;
+  }
+  if (a->grid_id == PDD_CV_NONE) {
+    lp->cv = 0;
+    lp->table = nullptr;
+    lp->grid_n = 0;
+  } else if (a->grid_id == PDD_CV_EXACT) {
+    lp->cv = 2;
+    lp->table = nullptr;
+    lp->grid_n = 0;
+  } else if (a->grid_id >= 0 && a->grid_id < PDD_MAX_GRIDS && p->grids[a->grid_id].table) {
+    lp->cv = 1;
+    lp->table = p->grids[a->grid_id].table;
+    lp->grid_n = p->grids[a->grid_id].n;
+  } else {
+    set_error("%s: level %d: grid_id %d is not a loaded grid", who, l, a->grid_id);
+    return PDD_ERR_INVALID;
+  }
+  if (a->n_nodes > 0)
+    for (int j = 0; j < dim; ++j)
+      if (!a->coords[j]) {
+        set_error("%s: level %d: coords[%d] is NULL", who, l, j);
+        return PDD_ERR_INVALID;
+      }
+  (void)out;
+  int64_t max_steps = p->desc.max_steps;
+  if (max_steps <= 0) {
+    const double ms = std::ceil(100.0 / a->dt);
+    max_steps = ms > 2.0e9 ? 2000000000ll : (int64_t)ms;
+  }
+  if (max_steps > 2000000000ll) max_steps = 2000000000ll;
+  lp->max_steps = max_steps;
+  return PDD_OK;
+}
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* b = (const unsigned char*)data;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+}  // namespace
+
+static int query_occupancy(pdd_problem* p, int grid_id, int threads, int* occ) {
+  const int cv = grid_id == PDD_CV_NONE ? 0 : (grid_id == PDD_CV_EXACT ? 2 : 1);
+  *occ = 0;
+  cudaError_t e = occupancy_paths(p->desc.kind, p->desc.precision, cv, false, threads, occ);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+  return PDD_OK;
+}
+
+static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* levels,
+                         pdd_node_stats* outs, uint32_t call_flags, const char* who) {
+  const int dim = p->dim;
+  const bool async = (call_flags & PDD_FLAG_ASYNC) != 0;
+  const bool graph = (call_flags & PDD_FLAG_GRAPH) != 0;
+  LevelPlan plan[PDD_MAX_LEVELS];
+  int cv_all = -1;
+  bool any_grid = false;
+  size_t total_nodes = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    int rc = check_level(p, &levels[l], &outs[l], who, l, &plan[l]);
+    if (rc != PDD_OK) return rc;
+    const bool host_io = !levels[l].coords_on_device || !outs[l].on_device;
+    if ((async || graph) && host_io) {
+      set_error("%s: PDD_FLAG_ASYNC / PDD_FLAG_GRAPH need device coordinates and outputs", who);
+      return PDD_ERR_INVALID;
+    }
+    if (plan[l].cv == 1) any_grid = true;
+    // one launch shares one control-variate mode: grids may mix with plain
+    // levels (no grid), the analytic gradient may not mix with either
+    const int cls = plan[l].cv == 2 ? 2 : 0;
+    if (cv_all < 0) cv_all = cls;
+    if (cv_all != cls) {
+      set_error("%s: levels mix the exact-gradient control variate with grids or plain levels",
+                who);
+      return PDD_ERR_INVALID;
+    }
+    total_nodes += (size_t)levels[l].n_nodes;
+  }
+  if (total_nodes >= (size_t)1 << 32) {
+    set_error("%s: more than 2^32 nodes in one call", who);
+    return PDD_ERR_INVALID;
+  }
+  const int cv = cv_all == 2 ? 2 : (any_grid ? 1 : 0);
+  if (total_nodes == 0) return PDD_OK;
+
+  pdd_ctx* c = p->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  if (!g.ok) {
+    set_error("%s: cannot select device %d", who, c->device);
+    return PDD_ERR_CUDA;
+  }
+  // workspace: header | records | staged coordinates | staged outputs
+  const size_t off_acc = 256;
+  size_t off = align_up(off_acc + total_nodes * kAccWords * 8, 256);
+  size_t coord_off[PDD_MAX_LEVELS], out_off[PDD_MAX_LEVELS];
+  for (int l = 0; l < n_levels; ++l) {
+    coord_off[l] = off;
+    if (!levels[l].coords_on_device) off += align_up((size_t)levels[l].n_nodes * 4, 256) * dim;
+  }
+  for (int l = 0; l < n_levels; ++l) {
+    out_off[l] = off;
+    if (!outs[l].on_device) off += 14 * align_up((size_t)levels[l].n_nodes * 8, 256);
+  }
+  int rc = ensure_workspace(c, off);
+  if (rc != PDD_OK) return rc;
+  char* ws = (char*)c->ws;
+  WsHeader* hdr = (WsHeader*)ws;
+  unsigned long long* acc = (unsigned long long*)(ws + off_acc);
+
+  // segments: levels with the smallest time step (the longest paths) first
+  int order[PDD_MAX_LEVELS];
+  for (int l = 0; l < n_levels; ++l) order[l] = l;
+  std::stable_sort(order, order + n_levels,
+                   [&](int x, int y) { return levels[x].dt < levels[y].dt; });
+  PathArgs pa{};
+  pa.cursor = &hdr->cursor;
+  pa.acc = acc;
+  pa.err = &hdr->err;
+  pa.trunc_total = &hdr->trunc_total;
+  pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
+  pa.max_blocks = c->max_blocks;
+  pa.block_threads = c->block_threads;
+  const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
+  uint32_t rec_base[PDD_MAX_LEVELS];
+  {
+    uint32_t rb = 0;
+    for (int l = 0; l < n_levels; ++l) {
+      rec_base[l] = rb;
+      rb += (uint32_t)levels[l].n_nodes;
+    }
+  }
+  unsigned long long begin = 0;
+  int ns = 0;
+  for (int oi = 0; oi < n_levels; ++oi) {
+    const int l = order[oi];
+    const pdd_estimate_args& a = levels[l];
+    if (a.n_nodes == 0) continue;
+    SegArgs& sg = pa.seg[ns++];
+    sg.cx = a.coords[0];
+    sg.cy = a.coords[1];
+    sg.cz = dim == 3 ? a.coords[2] : a.coords[0];
+    if (!a.coords_on_device) {
+      const float* dev[3];
+      for (int j = 0; j < dim; ++j)
+        dev[j] = (const float*)(ws + coord_off[l] + j * align_up((size_t)a.n_nodes * 4, 256));
+      sg.cx = dev[0];
+      sg.cy = dev[1];
+      sg.cz = dim == 3 ? dev[2] : dev[0];
+    }
+    sg.begin = begin;
+    sg.total = (unsigned long long)a.n_nodes * (unsigned long long)a.n_paths;
+    sg.n_paths = (unsigned long long)a.n_paths;
+    sg.grad = plan[l].table;
+    const bool emit = (a.flags & PDD_FLAG_EMIT_PATHS) != 0;
+    sg.emit_phi = emit ? a.path_phi : nullptr;
+    sg.emit_xi = emit ? a.path_xi : nullptr;
+    sg.emit_steps = emit ? a.path_steps : nullptr;
+    sg.h = a.dt;
+    sg.sqrt_h = std::sqrt(a.dt);
+    sg.thr0 = c0 * sg.sqrt_h;
+    sg.rec_base = rec_base[l];
+    sg.key0 = (uint32_t)a.seed;
+    sg.key1 = a.stream_tag;
+    sg.seed_hi = (uint32_t)(a.seed >> 32);
+    sg.grid_n = plan[l].grid_n;
+    sg.max_steps = (int)plan[l].max_steps;
+    begin += sg.total;
+  }
+  pa.n_segs = ns;
+  pa.total = begin;
+
+  StatPtrs sp[PDD_MAX_LEVELS];
+  for (int l = 0; l < n_levels; ++l) {
+    const pdd_node_stats& o = outs[l];
+    double* const user_d[12] = {o.mean_phi, o.var_phi, o.mean_cv, o.var_cv, o.cov_phi_xi,
+                                o.var_xi, o.rho, o.se_phi, o.se_cv, o.vr, o.pred_speedup,
+                                o.mean_steps};
+    uint64_t* const user_u[2] = {o.n_paths, o.n_truncated};
+    double* d[12];
+    unsigned long long* u[2];
+    const size_t n8 = align_up((size_t)levels[l].n_nodes * 8, 256);
+    for (int i = 0; i < 12; ++i)
+      d[i] = (!o.on_device && user_d[i]) ? (double*)(ws + out_off[l] + i * n8) : user_d[i];
+    for (int i = 0; i < 2; ++i)
+      u[i] = (!o.on_device && user_u[i]) ? (unsigned long long*)(ws + out_off[l] + (12 + i) * n8)
+                                         : (unsigned long long*)user_u[i];
+    sp[l] = StatPtrs{d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], d[8], d[9], d[10], d[11],
+                     u[0], u[1]};
+  }
+
+  // The launch sequence: clear the header and records, run every path, finalise
+  // every level.  With PDD_FLAG_GRAPH it is captured once into a CUDA graph and
+  // replayed while the arguments stay the same.
+  auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(ws, 0, off_acc + total_nodes * kAccWords * 8, st);
+    if (e != cudaSuccess) return e;
+    int blocks = 0;
+    e = launch_paths(p->desc.kind, p->desc.precision, cv, pa, c->num_sms, st, &blocks);
+    if (e != cudaSuccess) return e;
+    for (int l = 0; l < n_levels; ++l) {
+      if (levels[l].n_nodes == 0) continue;
+      const double kappa = levels[l].kappa > 0.0 ? levels[l].kappa : 1.0;
+      e = launch_finalize(acc + (size_t)rec_base[l] * kAccWords, (uint32_t)levels[l].n_nodes,
+                          kappa, sp[l], st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  int n_launch = 1;
+  for (int l = 0; l < n_levels; ++l) n_launch += levels[l].n_nodes > 0;
+
+  // host inputs
+  for (int l = 0; l < n_levels; ++l) {
+    const pdd_estimate_args& a = levels[l];
+    if (a.coords_on_device || a.n_nodes == 0) continue;
+    for (int j = 0; j < dim; ++j) {
+      float* dst = (float*)(ws + coord_off[l] + j * align_up((size_t)a.n_nodes * 4, 256));
+      PDD_CUDA(cudaMemcpyAsync(dst, a.coords[j], (size_t)a.n_nodes * 4, cudaMemcpyHostToDevice,
+                               c->stream),
+               "cudaMemcpyAsync(coords)");
+    }
+  }
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (c->timing) {
+    PDD_CUDA(cudaEventCreate(&ev0), "cudaEventCreate");
+    PDD_CUDA(cudaEventCreate(&ev1), "cudaEventCreate");
+  }
+  if (graph) {
+    uint64_t key = 1469598103934665603ull;
+    key = fnv1a(key, &p, sizeof(p));
+    key = fnv1a(key, &pa, sizeof(pa));
+    key = fnv1a(key, &n_levels, sizeof(n_levels));
+    key = fnv1a(key, sp, sizeof(StatPtrs) * n_levels);
+    for (int l = 0; l < n_levels; ++l) key = fnv1a(key, &levels[l].kappa, sizeof(double));
+    key = fnv1a(key, &c->ws, sizeof(c->ws));
+    if (!c->gexec || c->gkey != key) {
+      if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+      cudaGraph_t gr = nullptr;
+      PDD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal),
+               "cudaStreamBeginCapture");
+      cudaError_t e = enqueue(c->stream);
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+      if (e != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return cuda_fail(e, "graph capture");
+      }
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&c->gexec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return cuda_fail(e, "cudaGraphInstantiate");
+      }
+      c->gkey = key;
+      c->graph_captures += 1;
+    }
+    if (c->timing) PDD_CUDA(cudaEventRecord(ev0, c->stream), "cudaEventRecord");
+    PDD_CUDA(cudaGraphLaunch(c->gexec, c->stream), "cudaGraphLaunch");
+    if (c->timing) PDD_CUDA(cudaEventRecord(ev1, c->stream), "cudaEventRecord");
+  } else {
+    PDD_CUDA(cudaMemsetAsync(ws, 0, off_acc + total_nodes * kAccWords * 8, c->stream),
+             "cudaMemsetAsync");
+    if (c->timing) PDD_CUDA(cudaEventRecord(ev0, c->stream), "cudaEventRecord");
+    int blocks = 0;
+    PDD_CUDA(launch_paths(p->desc.kind, p->desc.precision, cv, pa, c->num_sms, c->stream, &blocks),
+             "path kernel launch");
+    if (c->timing) PDD_CUDA(cudaEventRecord(ev1, c->stream), "cudaEventRecord");
+    for (int l = 0; l < n_levels; ++l) {
+      if (levels[l].n_nodes == 0) continue;
+      const double kappa = levels[l].kappa > 0.0 ? levels[l].kappa : 1.0;
+      PDD_CUDA(launch_finalize(acc + (size_t)rec_base[l] * kAccWords,
+                               (uint32_t)levels[l].n_nodes, kappa, sp[l], c->stream),
+               "finalize launch");
+    }
+  }
+  if (c->timing) c->events.emplace_back(ev0, ev1);
+  c->launches += n_launch;
+  // host outputs
+  for (int l = 0; l < n_levels; ++l) {
+    const pdd_node_stats& o = outs[l];
+    if (o.on_device || levels[l].n_nodes == 0) continue;
+    const size_t nb = (size_t)levels[l].n_nodes * 8;
+    double* const user_d[12] = {o.mean_phi, o.var_phi, o.mean_cv, o.var_cv, o.cov_phi_xi,
+                                o.var_xi, o.rho, o.se_phi, o.se_cv, o.vr, o.pred_speedup,
+                                o.mean_steps};
+    uint64_t* const user_u[2] = {o.n_paths, o.n_truncated};
+    double* const dd[12] = {sp[l].mean_phi, sp[l].var_phi, sp[l].mean_cv, sp[l].var_cv,
+                            sp[l].cov_phi_xi, sp[l].var_xi, sp[l].rho, sp[l].se_phi,
+                            sp[l].se_cv, sp[l].vr, sp[l].pred_speedup, sp[l].mean_steps};
+    unsigned long long* const du[2] = {sp[l].n_paths, sp[l].n_truncated};
+    for (int i = 0; i < 12; ++i)
+      if (user_d[i])
+        PDD_CUDA(cudaMemcpyAsync(user_d[i], dd[i], nb, cudaMemcpyDeviceToHost, c->stream),
+                 "cudaMemcpyAsync(outputs)");
+    for (int i = 0; i < 2; ++i)
+      if (user_u[i])
+        PDD_CUDA(cudaMemcpyAsync(user_u[i], du[i], nb, cudaMemcpyDeviceToHost, c->stream),
+                 "cudaMemcpyAsync(outputs)");
+  }
+  if (async) return PDD_OK;
+  WsHeader h{};
+  PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+           "cudaMemcpyAsync(header)");
+  PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (h.err & kErrOverflow) {
+    set_error("%s: a score left the fixed-point range |score| < 32768", who);
+    return PDD_ERR_OVERFLOW;
+  }
+  if (h.cursor < pa.total) {
+    set_error("%s: internal error, %llu of %llu paths scheduled", who, h.cursor, pa.total);
+    return PDD_ERR_CUDA;
+  }
+  if (h.trunc_total > 0) {
+    set_error("%s: %llu paths hit max_steps", who, h.trunc_total);
+    return PDD_WARN_TRUNCATED;
+  }
+  (void)enqueue;
+  return PDD_OK;
+}
+
 extern "C" {
 
 int pdd_abi_version(void) { return PDD_ABI_VERSION; }
@@ -194,6 +567,7 @@ void pdd_ctx_destroy(pdd_ctx* c) {
       cudaEventDestroy(ev.first);
       cudaEventDestroy(ev.second);
     }
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->ws) cudaFree(c->ws);
     if (c->own_stream) cudaStreamDestroy(c->stream);
   }
@@ -257,6 +631,15 @@ int pdd_ctx_kernel_time(pdd_ctx* c, double* total_ms, int64_t* launches, double*
   *total_ms = tot;
   if (launches) *launches = n;
   return rc;
+}
+
+int pdd_ctx_graph_count(pdd_ctx* c, int64_t* captures) {
+  if (!c || !captures) {
+    set_error("pdd_ctx_graph_count: NULL argument");
+    return PDD_ERR_INVALID;
+  }
+  *captures = c->graph_captures;
+  return PDD_OK;
 }
 
 int pdd_ctx_launch_count(pdd_ctx* c, int64_t* launches) {
@@ -384,196 +767,137 @@ int pdd_estimate_nodes(pdd_problem* p, const pdd_estimate_args* a, pdd_node_stat
     set_error("pdd_estimate_nodes: NULL argument");
     return PDD_ERR_INVALID;
   }
-  const int dim = p->dim;
-  if (a->n_nodes < 0 || a->n_nodes >= (int64_t)1 << 32) {
-    set_error("pdd_estimate_nodes: n_nodes = %lld outside [0, 2^32)", (long long)a->n_nodes);
+  return estimate_impl(p, 1, a, out, a->flags & PDD_FLAG_ASYNC, "pdd_estimate_nodes");
+}
+
+int pdd_estimate_levels(pdd_problem* p, int n_levels, const pdd_estimate_args* levels,
+                        pdd_node_stats* outs, uint32_t flags) {
+  if (!p || !levels || !outs) {
+    set_error("pdd_estimate_levels: NULL argument");
     return PDD_ERR_INVALID;
   }
-  if (a->n_paths < 1 || a->n_paths >= (int64_t)1 << 32) {
-    set_error("pdd_estimate_nodes: n_paths = %lld outside [1, 2^32)", (long long)a->n_paths);
+  if (n_levels < 1 || n_levels > PDD_MAX_LEVELS) {
+    set_error("pdd_estimate_levels: n_levels = %d outside [1, %d]", n_levels, PDD_MAX_LEVELS);
     return PDD_ERR_INVALID;
   }
-  if (!(a->dt > 0.0) || !std::isfinite(a->dt)) {
-    set_error("pdd_estimate_nodes: dt must be finite and > 0");
+  if (flags & ~(PDD_FLAG_ASYNC | PDD_FLAG_GRAPH)) {
+    set_error("pdd_estimate_levels: unknown call flags 0x%x", flags);
     return PDD_ERR_INVALID;
   }
-  if ((unsigned long long)a->n_nodes * (unsigned long long)a->n_paths >= (1ull << 62)) {
-    set_error("pdd_estimate_nodes: n_nodes * n_paths too large");
-    return PDD_ERR_INVALID;
-  }
-  const bool emit = (a->flags & PDD_FLAG_EMIT_PATHS) != 0;
-  const bool async = (a->flags & PDD_FLAG_ASYNC) != 0;
-  if (a->flags & ~(PDD_FLAG_EMIT_PATHS | PDD_FLAG_ASYNC)) {
-    set_error("pdd_estimate_nodes: unknown flags 0x%x", a->flags);
-    return PDD_ERR_INVALID;
-  }
-  if (emit && (!a->path_phi || !a->path_xi || !a->path_steps)) {
-    set_error("pdd_estimate_nodes: EMIT_PATHS needs path_phi, path_xi and path_steps");
-    return PDD_ERR_INVALID;
-  }
-  if (async && (!a->coords_on_device || !out->on_device)) {
-    set_error("pdd_estimate_nodes: PDD_FLAG_ASYNC needs device coordinates and outputs");
-    return PDD_ERR_INVALID;
-  }
-  int cv = 0;  // kernel CV mode: 0 none, 1 grid, 2 exact
-  const void* table = nullptr;
-  int grid_n = 0;
-  if (a->grid_id == PDD_CV_NONE) {
-    cv = 0;
-  } else if (a->grid_id == PDD_CV_EXACT) {
-    cv = 2;
-  } else if (a->grid_id >= 0 && a->grid_id < PDD_MAX_GRIDS && p->grids[a->grid_id].table) {
-    cv = 1;
-    table = p->grids[a->grid_id].table;
-    grid_n = p->grids[a->grid_id].n;
-  } else {
-    set_error("pdd_estimate_nodes: grid_id %d is not a loaded grid", a->grid_id);
-    return PDD_ERR_INVALID;
-  }
-  if (a->n_nodes == 0) return PDD_OK;
-  for (int j = 0; j < dim; ++j)
-    if (!a->coords[j]) {
-      set_error("pdd_estimate_nodes: coords[%d] is NULL", j);
+  for (int l = 0; l < n_levels; ++l)
+    if (levels[l].flags & PDD_FLAG_ASYNC) {
+      set_error("pdd_estimate_levels: PDD_FLAG_ASYNC belongs to the call flags, not to level %d",
+                l);
       return PDD_ERR_INVALID;
     }
-  int64_t max_steps = p->desc.max_steps;
-  if (max_steps <= 0) {
-    const double ms = std::ceil(100.0 / a->dt);
-    max_steps = ms > 2.0e9 ? 2000000000ll : (int64_t)ms;
-  }
-  if (max_steps > 2000000000ll) max_steps = 2000000000ll;
+  return estimate_impl(p, n_levels, levels, outs, flags, "pdd_estimate_levels");
+}
 
-  pdd_ctx* c = p->ctx;
-  std::lock_guard<std::mutex> lk(c->mu);
-  DeviceGuard g(c->device);
-  if (!g.ok) {
-    set_error("pdd_estimate_nodes: cannot select device %d", c->device);
-    return PDD_ERR_CUDA;
+int pdd_ctx_set_launch(pdd_ctx* c, int block_threads, int max_blocks) {
+  if (!c) {
+    set_error("pdd_ctx_set_launch: NULL context");
+    return PDD_ERR_INVALID;
   }
-  const size_t n = (size_t)a->n_nodes;
-  // workspace layout
-  const size_t off_acc = 256;
-  const size_t off_coords = align_up(off_acc + n * kAccWords * 8, 256);
-  const size_t coords_bytes = a->coords_on_device ? 0 : align_up(n * 4, 256) * dim;
-  const size_t off_out = off_coords + coords_bytes;
-  const size_t out_bytes = out->on_device ? 0 : 14 * align_up(n * 8, 256);
-  int rc = ensure_workspace(c, off_out + out_bytes);
-  if (rc != PDD_OK) return rc;
-  char* ws = (char*)c->ws;
-  WsHeader* hdr = (WsHeader*)ws;
-  unsigned long long* acc = (unsigned long long*)(ws + off_acc);
-  PDD_CUDA(cudaMemsetAsync(ws, 0, off_acc + n * kAccWords * 8, c->stream), "cudaMemsetAsync");
-  const float* coords[3] = {a->coords[0], a->coords[1], dim == 3 ? a->coords[2] : nullptr};
-  if (!a->coords_on_device) {
-    for (int j = 0; j < dim; ++j) {
-      float* dst = (float*)(ws + off_coords + j * align_up(n * 4, 256));
-      PDD_CUDA(cudaMemcpyAsync(dst, a->coords[j], n * 4, cudaMemcpyHostToDevice, c->stream),
-               "cudaMemcpyAsync(coords)");
-      coords[j] = dst;
+  if (block_threads != 0 && (block_threads < 32 || block_threads > 512 || block_threads % 32)) {
+    set_error("pdd_ctx_set_launch: block_threads = %d must be 0 or a multiple of 32 in [32, 512]",
+              block_threads);
+    return PDD_ERR_INVALID;
+  }
+  if (max_blocks < 0) {
+    set_error("pdd_ctx_set_launch: max_blocks = %d must be >= 0", max_blocks);
+    return PDD_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->block_threads = block_threads;
+  c->max_blocks = max_blocks;
+  return PDD_OK;
+}
+
+int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_threads,
+                 int* best_max_blocks, double* best_ms) {
+  if (!p || !sample) {
+    set_error("pdd_autotune: NULL argument");
+    return PDD_ERR_INVALID;
+  }
+  if (!sample->coords_on_device) {
+    set_error("pdd_autotune: the sample must use device coordinates");
+    return PDD_ERR_INVALID;
+  }
+  pdd_ctx* c = p->ctx;
+  const int old_threads = c->block_threads, old_blocks = c->max_blocks;
+  const size_t n = (size_t)sample->n_nodes;
+  if (n == 0) {
+    set_error("pdd_autotune: empty sample");
+    return PDD_ERR_INVALID;
+  }
+  // device outputs: the means only (the other statistics are not needed here)
+  double* dmean = nullptr;
+  {
+    DeviceGuard g(c->device);
+    PDD_CUDA(cudaMalloc(&dmean, n * sizeof(double)), "cudaMalloc(autotune)");
+  }
+  pdd_node_stats out{};
+  out.on_device = 1;
+  out.mean_phi = dmean;
+  pdd_estimate_args a = *sample;
+  a.flags &= ~(PDD_FLAG_EMIT_PATHS | PDD_FLAG_ASYNC);
+  const int threads_c[3] = {128, 256, 512};
+  int bt = 0, bb = 0;
+  double bms = 1e300;
+  int rc = PDD_OK;
+  for (int ti = 0; ti < 3 && rc >= 0; ++ti) {
+    // full occupancy, and half of it (fewer resident warps, less L1 pressure)
+    for (int frac = 0; frac < 2 && rc >= 0; ++frac) {
+      int max_blocks = 0;
+      if (frac == 1) {
+        int occ = 0;
+        rc = query_occupancy(p, a.grid_id, threads_c[ti], &occ);
+        if (rc < 0) break;
+        max_blocks = (occ / 2 > 0 ? occ / 2 : 1) * c->num_sms;
+      }
+      pdd_ctx_set_launch(c, threads_c[ti], max_blocks);
+      double ms = 0.0;
+      for (int rep = 0; rep < 2 && rc >= 0; ++rep) {  // first run warms up
+        double t0 = 0.0;
+        cudaEvent_t e0, e1;
+        {
+          DeviceGuard g(c->device);
+          cudaEventCreate(&e0);
+          cudaEventCreate(&e1);
+          cudaEventRecord(e0, c->stream);
+        }
+        rc = pdd_estimate_nodes(p, &a, &out);
+        {
+          DeviceGuard g(c->device);
+          cudaEventRecord(e1, c->stream);
+          cudaEventSynchronize(e1);
+          float f = 0.f;
+          cudaEventElapsedTime(&f, e0, e1);
+          t0 = f;
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+        }
+        ms = t0;
+      }
+      if (rc >= 0 && ms < bms) {
+        bms = ms;
+        bt = threads_c[ti];
+        bb = max_blocks;
+      }
     }
   }
-  PathArgs pa{};
-  pa.cx = coords[0];
-  pa.cy = coords[1];
-  pa.cz = coords[2] ? coords[2] : coords[0];
-  pa.total = (unsigned long long)n * (unsigned long long)a->n_paths;
-  pa.n_paths = (unsigned long long)a->n_paths;
-  pa.cursor = &hdr->cursor;
-  pa.acc = acc;
-  pa.err = &hdr->err;
-  pa.trunc_total = &hdr->trunc_total;
-  pa.emit_phi = emit ? a->path_phi : nullptr;
-  pa.emit_xi = emit ? a->path_xi : nullptr;
-  pa.emit_steps = emit ? a->path_steps : nullptr;
-  pa.grad = table;
-  pa.grid_n = grid_n;
-  pa.max_steps = (int)max_steps;
-  pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
-  pa.max_blocks = 0;
-  pa.h = a->dt;
-  pa.sqrt_h = std::sqrt(a->dt);
-  const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
-  pa.thr0 = c0 * pa.sqrt_h;
-  pa.key0 = (uint32_t)a->seed;
-  pa.key1 = a->stream_tag;
-  pa.seed_hi = (uint32_t)(a->seed >> 32);
-
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  if (c->timing) {
-    PDD_CUDA(cudaEventCreate(&ev0), "cudaEventCreate");
-    PDD_CUDA(cudaEventCreate(&ev1), "cudaEventCreate");
-    PDD_CUDA(cudaEventRecord(ev0, c->stream), "cudaEventRecord");
+  {
+    DeviceGuard g(c->device);
+    cudaFree(dmean);
   }
-  int blocks = 0;
-  PDD_CUDA(launch_paths(p->desc.kind, p->desc.precision, cv, pa, c->num_sms, c->stream, &blocks),
-           "path kernel launch");
-  c->launches += 1;
-  if (c->timing) {
-    PDD_CUDA(cudaEventRecord(ev1, c->stream), "cudaEventRecord");
-    c->events.emplace_back(ev0, ev1);
+  if (rc < 0) {
+    pdd_ctx_set_launch(c, old_threads, old_blocks);
+    return rc;
   }
-  StatPtrs sp{};
-  double* dptr[12];
-  unsigned long long* uptr[2];
-  double* const* user_d[12] = {&out->mean_phi, &out->var_phi, &out->mean_cv, &out->var_cv,
-                               &out->cov_phi_xi, &out->var_xi, &out->rho, &out->se_phi,
-                               &out->se_cv, &out->vr, &out->pred_speedup, &out->mean_steps};
-  uint64_t* const* user_u[2] = {&out->n_paths, &out->n_truncated};
-  for (int i = 0; i < 12; ++i) {
-    dptr[i] = *user_d[i];
-    if (!out->on_device && dptr[i]) dptr[i] = (double*)(ws + off_out + i * align_up(n * 8, 256));
-  }
-  for (int i = 0; i < 2; ++i) {
-    uptr[i] = (unsigned long long*)*user_u[i];
-    if (!out->on_device && uptr[i])
-      uptr[i] = (unsigned long long*)(ws + off_out + (12 + i) * align_up(n * 8, 256));
-  }
-  sp.mean_phi = dptr[0];
-  sp.var_phi = dptr[1];
-  sp.mean_cv = dptr[2];
-  sp.var_cv = dptr[3];
-  sp.cov_phi_xi = dptr[4];
-  sp.var_xi = dptr[5];
-  sp.rho = dptr[6];
-  sp.se_phi = dptr[7];
-  sp.se_cv = dptr[8];
-  sp.vr = dptr[9];
-  sp.pred_speedup = dptr[10];
-  sp.mean_steps = dptr[11];
-  sp.n_paths = uptr[0];
-  sp.n_truncated = uptr[1];
-  const double kappa = a->kappa > 0.0 ? a->kappa : 1.0;
-  PDD_CUDA(launch_finalize(acc, (uint32_t)n, kappa, sp, c->stream), "finalize launch");
-  c->launches += 1;
-  if (!out->on_device) {
-    for (int i = 0; i < 12; ++i)
-      if (*user_d[i])
-        PDD_CUDA(cudaMemcpyAsync(*user_d[i], dptr[i], n * 8, cudaMemcpyDeviceToHost, c->stream),
-                 "cudaMemcpyAsync(outputs)");
-    for (int i = 0; i < 2; ++i)
-      if (*user_u[i])
-        PDD_CUDA(cudaMemcpyAsync(*user_u[i], uptr[i], n * 8, cudaMemcpyDeviceToHost, c->stream),
-                 "cudaMemcpyAsync(outputs)");
-  }
-  if (async) return PDD_OK;
-  WsHeader h{};
-  PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
-           "cudaMemcpyAsync(header)");
-  PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-  if (h.err & kErrOverflow) {
-    set_error("pdd_estimate_nodes: a score left the fixed-point range |score| < 32768");
-    return PDD_ERR_OVERFLOW;
-  }
-  if (h.cursor < pa.total) {
-    set_error("pdd_estimate_nodes: internal error, %llu of %llu paths scheduled", h.cursor,
-              pa.total);
-    return PDD_ERR_CUDA;
-  }
-  if (h.trunc_total > 0) {
-    set_error("pdd_estimate_nodes: %llu paths hit max_steps = %lld", h.trunc_total,
-              (long long)max_steps);
-    return PDD_WARN_TRUNCATED;
-  }
+  pdd_ctx_set_launch(c, bt, bb);
+  if (best_threads) *best_threads = bt;
+  if (best_max_blocks) *best_max_blocks = bb;
+  if (best_ms) *best_ms = bms;
   return PDD_OK;
 }
 

@@ -15,29 +15,42 @@ constexpr unsigned kErrOverflow = 1u;       // a score left the fixed-point rang
 constexpr int kAccWords = 16;               // 64-bit words per node record
 constexpr unsigned long long kWarpBatch = 32;  // path indices a warp takes per cursor grab
 
-// Arguments of one path-kernel launch (passed by value as a grid constant).
-struct PathArgs {
+constexpr int kMaxSegments = 32;           // segments (levels / requests) per launch
+
+// One segment of a launch: n_nodes x n_paths paths with their own nodes,
+// time step, control grid, random-stream key and output records.
+struct SegArgs {
   const float* cx;
   const float* cy;
   const float* cz;
+  unsigned long long begin;    // first index of the segment in the launch's flat path space
   unsigned long long total;    // n_nodes * n_paths
   unsigned long long n_paths;
-  unsigned long long* cursor;  // flat path cursor, zeroed before the launch
-  unsigned long long* acc;     // n_nodes x 16 words of exact sums, zeroed
-  unsigned* err;               // error bits (kErr*)
-  unsigned long long* trunc_total;
-  float* emit_phi;             // optional per-path outputs
+  const void* grad;            // float2 (2D) / float4 (3D) gradient table; null: no grid
+  float* emit_phi;             // optional per-path outputs (node-major within the segment)
   float* emit_xi;
   int* emit_steps;
-  const void* grad;            // float2 (2D) / float4 (3D) gradient table
-  int grid_n;
-  int max_steps;
-  int y_exp;
-  int max_blocks;              // 0 = occupancy x SM count
   double h;
   double sqrt_h;
   double thr0;                 // c0 sqrt(h)
+  uint32_t rec_base;           // first node record of the segment
   uint32_t key0, key1, seed_hi;
+  int grid_n;
+  int max_steps;
+};
+
+// Arguments of one path-kernel launch (passed by value as a grid constant).
+struct PathArgs {
+  unsigned long long total;    // sum of the segments' totals
+  unsigned long long* cursor;  // flat path cursor, zeroed before the launch
+  unsigned long long* acc;     // node records (16 words of exact sums each), zeroed
+  unsigned* err;               // error bits (kErr*)
+  unsigned long long* trunc_total;
+  int y_exp;
+  int max_blocks;              // 0 = occupancy x SM count
+  int block_threads;           // 0 = default (256)
+  int n_segs;                  // 1 .. kMaxSegments; segments in increasing `begin`
+  SegArgs seg[kMaxSegments];
 };
 
 // Per-node output pointers (device; any may be null).
@@ -76,6 +89,9 @@ bool problem_view(pdd_problem* p, ProblemView* v);
 
 cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int num_sms,
                          cudaStream_t st, int* blocks);
+// Resident blocks per SM of the path kernel of (kind, precision, cv, multi) at
+// `threads` threads per block.
+cudaError_t occupancy_paths(int kind, int precision, int cv, bool multi, int threads, int* occ);
 cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, double kappa,
                             const StatPtrs& out, cudaStream_t st);
 // Gradient table of grid values v (FP64, n^D, x fastest) into float2/float4.

@@ -152,30 +152,36 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   if (e != cudaSuccess) return fail(e, "cudaMemsetAsync");
 
   PathArgs pa{};
-  pa.cx = a->coords[0];
-  pa.cy = a->coords[1];
-  pa.cz = pv.dim == 3 ? a->coords[2] : a->coords[0];
   pa.total = (unsigned long long)n * (unsigned long long)a->n_paths;
-  pa.n_paths = (unsigned long long)a->n_paths;
   pa.cursor = &hdr->cursor;
   pa.acc = acc;
   pa.err = &hdr->err;
   pa.trunc_total = &hdr->trunc_total;
-  pa.emit_phi = emit ? a->path_phi : nullptr;
-  pa.emit_xi = emit ? a->path_xi : nullptr;
-  pa.emit_steps = emit ? a->path_steps : nullptr;
-  pa.grad = table;
-  pa.grid_n = grid_n;
-  pa.max_steps = (int)max_steps;
   pa.y_exp = pv.y_rule == PDD_Y_EXP;
   pa.max_blocks = 0;
-  pa.h = a->dt;
-  pa.sqrt_h = std::sqrt(a->dt);
+  pa.block_threads = 0;
+  pa.n_segs = 1;
+  SegArgs& sg = pa.seg[0];
+  sg.cx = a->coords[0];
+  sg.cy = a->coords[1];
+  sg.cz = pv.dim == 3 ? a->coords[2] : a->coords[0];
+  sg.begin = 0;
+  sg.total = pa.total;
+  sg.n_paths = (unsigned long long)a->n_paths;
+  sg.grad = table;
+  sg.emit_phi = emit ? a->path_phi : nullptr;
+  sg.emit_xi = emit ? a->path_xi : nullptr;
+  sg.emit_steps = emit ? a->path_steps : nullptr;
+  sg.h = a->dt;
+  sg.sqrt_h = std::sqrt(a->dt);
   const double c0 = pv.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
-  pa.thr0 = c0 * pa.sqrt_h;
-  pa.key0 = (uint32_t)a->seed;
-  pa.key1 = a->stream_tag;
-  pa.seed_hi = (uint32_t)(a->seed >> 32);
+  sg.thr0 = c0 * sg.sqrt_h;
+  sg.rec_base = 0;
+  sg.key0 = (uint32_t)a->seed;
+  sg.key1 = a->stream_tag;
+  sg.seed_hi = (uint32_t)(a->seed >> 32);
+  sg.grid_n = grid_n;
+  sg.max_steps = (int)max_steps;
   int blocks = 0;
   e = launch_paths(pv.kind, pv.precision, cv, pa, pv.num_sms, pv.stream, &blocks);
   if (e != cudaSuccess) return fail(e, "path kernel launch");

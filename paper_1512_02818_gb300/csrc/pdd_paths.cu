@@ -24,7 +24,8 @@
 
 namespace pdd {
 
-constexpr int kBlockThreads = 256;
+constexpr int kBlockThreads = 256;     // default block size
+constexpr int kMaxBlockThreads = 512;  // largest block size a launch may ask for
 #ifndef PDD_MIN_BLOCKS
 #define PDD_MIN_BLOCKS 1
 #endif
@@ -37,27 +38,55 @@ struct PathState {
   T x[3];
   T Y, Z, Zc, XI, XIc;
   int k;
-  uint32_t node, path;
+  uint32_t node, path, seg;
 };
 
-// Start path g of the flat index space.
-template <class T, int D>
+// Per-lane copy of the parameters of the segment the lane's path belongs to.
+// With a single segment they are the same for every lane and never change.
+template <class T>
+struct LaneSeg {
+  T h, sqh, thr0;
+  const void* grad;
+  int gn, max_steps;
+};
+
+template <class T>
+__device__ __forceinline__ void load_seg(const SegArgs& sg, LaneSeg<T>& ls) {
+  ls.h = (T)sg.h;
+  ls.sqh = (T)sg.sqrt_h;
+  ls.thr0 = (T)sg.thr0;
+  ls.grad = sg.grad;
+  ls.gn = sg.grid_n;
+  ls.max_steps = sg.max_steps;
+}
+
+// Start path g of the launch's flat index space.
+template <class T, int D, bool MULTI>
 __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long g,
-                                           PathState<T>& s) {
-  if (a.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
-    const uint32_t gg = (uint32_t)g, np = (uint32_t)a.n_paths;
+                                           PathState<T>& s, LaneSeg<T>& ls) {
+  uint32_t si = 0;
+  if (MULTI) {
+    for (int i = 1; i < a.n_segs; ++i)
+      if (g >= a.seg[i].begin) si = (uint32_t)i;
+  }
+  const SegArgs& sg = a.seg[si];
+  const unsigned long long li = g - sg.begin;
+  if (sg.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
+    const uint32_t gg = (uint32_t)li, np = (uint32_t)sg.n_paths;
     s.node = gg / np;
     s.path = gg - s.node * np;
   } else {
-    s.node = (uint32_t)(g / a.n_paths);
-    s.path = (uint32_t)(g - (unsigned long long)s.node * a.n_paths);
+    s.node = (uint32_t)(li / sg.n_paths);
+    s.path = (uint32_t)(li - (unsigned long long)s.node * sg.n_paths);
   }
-  s.x[0] = (T)__ldg(a.cx + s.node);
-  s.x[1] = (T)__ldg(a.cy + s.node);
-  s.x[2] = (D == 3) ? (T)__ldg(a.cz + s.node) : T(0);
+  s.seg = si;
+  s.x[0] = (T)__ldg(sg.cx + s.node);
+  s.x[1] = (T)__ldg(sg.cy + s.node);
+  s.x[2] = (D == 3) ? (T)__ldg(sg.cz + s.node) : T(0);
   s.Y = T(1);
   s.Z = s.Zc = s.XI = s.XIc = T(0);
   s.k = 0;
+  if (MULTI) load_seg(sg, ls);
 }
 
 // Finish test of Algorithm 1: d(X_k) >= -c0 |sigma^T N| sqrt(h).
@@ -69,11 +98,20 @@ __device__ __forceinline__ bool should_finish(const PathState<T>& s, T thr0) {
   return m <= thr;
 }
 
+// Philox block `blk` of the lane's path.
+template <bool MULTI>
+__device__ __forceinline__ uint4 path_block(const PathArgs& a, uint32_t seg, uint32_t blk,
+                                            uint32_t path, uint32_t node) {
+  const SegArgs& sg = a.seg[MULTI ? seg : 0];
+  return philox4x32_10(make_uint4(blk, path, node, sg.seed_hi), make_uint2(sg.key0, sg.key1));
+}
+
 // One Euler-Maruyama step (eq. F:E_M) with the Feynman-Kac weights and the
-// control variate, all right-hand sides at X_k.
-template <class P, class T, int D, int CV>
-__device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s, T h,
-                                           const T* dW) {
+// control variate, all right-hand sides at X_k.  dW holds sqrt(h) * normals.
+template <class P, class T, int D, int CV, bool MULTI>
+__device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
+                                           const LaneSeg<T>& ls, const T* dW) {
+  const T h = ls.h;
   Coef<T> o;
   P::template eval<T, CV == kCvExact>(s.x[0], s.x[1], s.x[2], o);
   T sdW[3];
@@ -86,13 +124,14 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s, T
     sdW[1] = dW1;
   }
   sdW[2] = (D == 3) ? dW[2] : T(0);
-  if (CV != kCvNone) {
+  // with several segments a segment without a grid runs the plain estimator
+  if (CV != kCvNone && (CV != kCvGrid || !MULTI || ls.grad != nullptr)) {
     T gv[3] = {T(0), T(0), T(0)};
     if (CV == kCvGrid) {
       if (D == 2)
-        grid_grad_2d<T>((const float2*)a.grad, a.grid_n, s.x[0], s.x[1], gv[0], gv[1]);
+        grid_grad_2d<T>((const float2*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1]);
       else
-        grid_grad_3d<T>((const float4*)a.grad, a.grid_n, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
+        grid_grad_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
                         gv[2]);
     } else {
       gv[0] = o.g0;
@@ -113,7 +152,7 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s, T
 
 // Exit scoring: X_tau = Pi(X_k), phi = g(X_tau) Y + Z, xi, and the exact
 // fixed-point accumulation into the node record.
-template <class P, class T, int D>
+template <class P, class T, int D, bool MULTI>
 __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T>& s, bool trunc) {
   T p[3] = {s.x[0], s.x[1], s.x[2]};
   project_box<T>(p, D);
@@ -124,7 +163,8 @@ __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T
   long long qa, qb;
   const bool ok = to_fixed(phi, qa) & to_fixed(psi, qb);
   if (!ok) atomicOr(a.err, kErrOverflow);
-  unsigned long long* w = a.acc + (size_t)s.node * kAccWords;
+  const SegArgs& sg = a.seg[MULTI ? s.seg : 0];
+  unsigned long long* w = a.acc + (size_t)(sg.rec_base + s.node) * kAccWords;
   atomic_add_s64(w + 0, qa);
   atomic_add_prod(w + 2, qa, qa);
   atomic_add_s64(w + 4, qb);
@@ -138,21 +178,21 @@ __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T
     atomicAdd(w + 15, 1ull);
     atomicAdd(a.trunc_total, 1ull);
   }
-  if (a.emit_phi != nullptr) {
-    const size_t i = (size_t)s.node * a.n_paths + s.path;
-    a.emit_phi[i] = (float)phi;
-    a.emit_xi[i] = (float)xi;
-    a.emit_steps[i] = s.k;
+  if (sg.emit_phi != nullptr) {
+    const size_t i = (size_t)s.node * sg.n_paths + s.path;
+    sg.emit_phi[i] = (float)phi;
+    sg.emit_xi[i] = (float)xi;
+    sg.emit_steps[i] = s.k;
   }
 }
 
 // Refill idle lanes from the warp's batch; returns false when no lane of the
 // warp has a path left to run.  All arguments except the lane state are
 // warp-uniform.
-template <class T, int D>
-__device__ __forceinline__ bool refill(const PathArgs& a, PathState<T>& s, bool& active,
-                                       unsigned long long& bnext, unsigned long long& bend,
-                                       bool& exhausted) {
+template <class T, int D, bool MULTI>
+__device__ __forceinline__ bool refill(const PathArgs& a, PathState<T>& s, LaneSeg<T>& ls,
+                                       bool& active, unsigned long long& bnext,
+                                       unsigned long long& bend, bool& exhausted) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
   unsigned idle = __ballot_sync(kFull, !active);
@@ -171,7 +211,7 @@ __device__ __forceinline__ bool refill(const PathArgs& a, PathState<T>& s, bool&
     const unsigned avail = (unsigned)min(bend - bnext, 32ull);
     const unsigned rank = __popc(idle & lt);
     if (!active && rank < avail) {
-      start_path<T, D>(a, bnext + rank, s);
+      start_path<T, D, MULTI>(a, bnext + rank, s, ls);
       active = true;
     }
     bnext += min((unsigned)__popc(idle), avail);
@@ -180,39 +220,45 @@ __device__ __forceinline__ bool refill(const PathArgs& a, PathState<T>& s, bool&
   return __ballot_sync(kFull, active) != 0u;
 }
 
-template <class P, class T, int CV>
-__global__ void __launch_bounds__(kBlockThreads, PDD_MIN_BLOCKS) paths_2d(const __grid_constant__ PathArgs a) {
-  const T h = (T)a.h, sqh = (T)a.sqrt_h, thr0 = (T)a.thr0;
-  const uint2 key = make_uint2(a.key0, a.key1);
-  PathState<T> s;
+template <class T>
+__device__ __forceinline__ void init_lane(const PathArgs& a, PathState<T>& s, LaneSeg<T>& ls) {
   s.x[0] = s.x[1] = s.x[2] = T(0);
   s.Y = s.Z = s.Zc = s.XI = s.XIc = T(0);
   s.k = 0;
-  s.node = s.path = 0;
+  s.node = s.path = s.seg = 0;
+  load_seg(a.seg[0], ls);
+}
+
+template <class P, class T, int CV, bool MULTI>
+__global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS)
+    paths_2d(const __grid_constant__ PathArgs a) {
+  PathState<T> s;
+  LaneSeg<T> ls;
+  init_lane(a, s, ls);
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
-  while (refill<T, 2>(a, s, active, bnext, bend, exhausted)) {
+  while (refill<T, 2, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
     bool fin = false, trunc = false;
     uint4 w = make_uint4(0, 0, 0, 0);
-    if (active) fin = should_finish<P, T, 2>(s, thr0);
+    if (active) fin = should_finish<P, T, 2>(s, ls.thr0);
     if (active && !fin) {
-      w = philox4x32_10(make_uint4((uint32_t)(s.k >> 1), s.path, s.node, a.seed_hi), key);
+      w = path_block<MULTI>(a, s.seg, (uint32_t)(s.k >> 1), s.path, s.node);
       T n[3];
-      box_muller(w.x, w.y, n[0], n[1], sqh);
+      box_muller(w.x, w.y, n[0], n[1], ls.sqh);
       n[2] = T(0);
-      euler_step<P, T, 2, CV>(a, s, h, n);
-      if (s.k >= a.max_steps) fin = trunc = true;
+      euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
     }
-    if (active && !fin) fin = should_finish<P, T, 2>(s, thr0);
+    if (active && !fin) fin = should_finish<P, T, 2>(s, ls.thr0);
     if (active && !fin) {
       T n[3];
-      box_muller(w.z, w.w, n[0], n[1], sqh);
+      box_muller(w.z, w.w, n[0], n[1], ls.sqh);
       n[2] = T(0);
-      euler_step<P, T, 2, CV>(a, s, h, n);
-      if (s.k >= a.max_steps) fin = trunc = true;
+      euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
     }
     if (active && fin) {
-      finish_path<P, T, 2>(a, s, trunc);
+      finish_path<P, T, 2, MULTI>(a, s, trunc);
       active = false;
     }
   }
@@ -222,64 +268,61 @@ __global__ void __launch_bounds__(kBlockThreads, PDD_MIN_BLOCKS) paths_2d(const 
 // 3j+1, 3j+2 (words a0..a3, b0..b3, c0..c3):
 //   step 0: a0 a1 a2   step 1: a3 b0 b1   step 2: b2 b3 c0   step 3: c1 c2 c3
 // Blocks are drawn only when the path is still running.
-template <class P, class T, int CV>
-__global__ void __launch_bounds__(kBlockThreads, PDD_MIN_BLOCKS) paths_3d(const __grid_constant__ PathArgs a) {
-  const T h = (T)a.h, sqh = (T)a.sqrt_h, thr0 = (T)a.thr0;
-  const uint2 key = make_uint2(a.key0, a.key1);
+template <class P, class T, int CV, bool MULTI>
+__global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS)
+    paths_3d(const __grid_constant__ PathArgs a) {
   PathState<T> s;
-  s.x[0] = s.x[1] = s.x[2] = T(0);
-  s.Y = s.Z = s.Zc = s.XI = s.XIc = T(0);
-  s.k = 0;
-  s.node = s.path = 0;
+  LaneSeg<T> ls;
+  init_lane(a, s, ls);
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
-  while (refill<T, 3>(a, s, active, bnext, bend, exhausted)) {
+  while (refill<T, 3, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
     bool fin = false, trunc = false;
     T carry0 = T(0), carry1 = T(0);  // normals left over from the previous block
     uint4 w = make_uint4(0, 0, 0, 0);
     const uint32_t blk0 = 3u * ((uint32_t)s.k >> 2);
     // step 0
-    if (active) fin = should_finish<P, T, 3>(s, thr0);
+    if (active) fin = should_finish<P, T, 3>(s, ls.thr0);
     if (active && !fin) {
-      w = philox4x32_10(make_uint4(blk0, s.path, s.node, a.seed_hi), key);
+      w = path_block<MULTI>(a, s.seg, blk0, s.path, s.node);
       T n[3], n3;
-      box_muller(w.x, w.y, n[0], n[1], sqh);
-      box_muller(w.z, w.w, n[2], n3, sqh);
+      box_muller(w.x, w.y, n[0], n[1], ls.sqh);
+      box_muller(w.z, w.w, n[2], n3, ls.sqh);
       carry0 = n3;
-      euler_step<P, T, 3, CV>(a, s, h, n);
-      if (s.k >= a.max_steps) fin = trunc = true;
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
     }
     // step 1
-    if (active && !fin) fin = should_finish<P, T, 3>(s, thr0);
+    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
     if (active && !fin) {
-      w = philox4x32_10(make_uint4(blk0 + 1u, s.path, s.node, a.seed_hi), key);
+      w = path_block<MULTI>(a, s.seg, blk0 + 1u, s.path, s.node);
       T n[3];
       n[0] = carry0;
-      box_muller(w.x, w.y, n[1], n[2], sqh);
-      euler_step<P, T, 3, CV>(a, s, h, n);
-      if (s.k >= a.max_steps) fin = trunc = true;
+      box_muller(w.x, w.y, n[1], n[2], ls.sqh);
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
     }
     // step 2
-    if (active && !fin) fin = should_finish<P, T, 3>(s, thr0);
+    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
     if (active && !fin) {
       T n[3];
-      box_muller(w.z, w.w, n[0], n[1], sqh);
-      w = philox4x32_10(make_uint4(blk0 + 2u, s.path, s.node, a.seed_hi), key);
-      box_muller(w.x, w.y, n[2], carry1, sqh);
-      euler_step<P, T, 3, CV>(a, s, h, n);
-      if (s.k >= a.max_steps) fin = trunc = true;
+      box_muller(w.z, w.w, n[0], n[1], ls.sqh);
+      w = path_block<MULTI>(a, s.seg, blk0 + 2u, s.path, s.node);
+      box_muller(w.x, w.y, n[2], carry1, ls.sqh);
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
     }
     // step 3
-    if (active && !fin) fin = should_finish<P, T, 3>(s, thr0);
+    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
     if (active && !fin) {
       T n[3];
       n[0] = carry1;
-      box_muller(w.z, w.w, n[1], n[2], sqh);
-      euler_step<P, T, 3, CV>(a, s, h, n);
-      if (s.k >= a.max_steps) fin = trunc = true;
+      box_muller(w.z, w.w, n[1], n[2], ls.sqh);
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
     }
     if (active && fin) {
-      finish_path<P, T, 3>(a, s, trunc);
+      finish_path<P, T, 3, MULTI>(a, s, trunc);
       active = false;
     }
   }
@@ -326,56 +369,103 @@ __global__ void finalize_nodes(const unsigned long long* __restrict__ acc, uint3
 // ---------------------------------------------------------------------------
 // Launch dispatch.
 // ---------------------------------------------------------------------------
-template <class P, class T, int CV>
+template <class P, class T, int CV, bool MULTI>
 static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, int* blocks) {
   void (*kern)(PathArgs);
   if constexpr (P::kDim == 3)
-    kern = paths_3d<P, T, CV>;
+    kern = paths_3d<P, T, CV, MULTI>;
   else
-    kern = paths_2d<P, T, CV>;
-  static int per_sm = 0;  // occupancy of this instantiation (same for every device here)
-  if (per_sm == 0) {
+    kern = paths_2d<P, T, CV, MULTI>;
+  const int threads = a.block_threads > 0 ? a.block_threads : kBlockThreads;
+  if (threads % 32 != 0 || threads > kMaxBlockThreads) return cudaErrorInvalidValue;
+  // occupancy of this instantiation per block size (same for every device here)
+  static int per_sm[kMaxBlockThreads / 32 + 1] = {0};
+  int& occ = per_sm[threads / 32];
+  if (occ == 0) {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kBlockThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, 0);
     if (e != cudaSuccess) return e;
-    per_sm = v > 0 ? v : 1;
+    occ = v > 0 ? v : 1;
   }
   const unsigned long long warps_needed = (a.total + 31ull) / 32ull;
   const unsigned long long blocks_needed =
-      (warps_needed + (kBlockThreads / 32) - 1) / (kBlockThreads / 32);
-  unsigned long long nb = (unsigned long long)per_sm * (unsigned long long)num_sms;
+      (warps_needed + (threads / 32) - 1) / (threads / 32);
+  unsigned long long nb = (unsigned long long)occ * (unsigned long long)num_sms;
   if (a.max_blocks > 0 && nb > (unsigned long long)a.max_blocks) nb = a.max_blocks;
   if (nb > blocks_needed) nb = blocks_needed;
   if (nb < 1) nb = 1;
   *blocks = (int)nb;
-  kern<<<(unsigned)nb, kBlockThreads, 0, st>>>(a);
+  kern<<<(unsigned)nb, (unsigned)threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-template <class P, class T>
-static cudaError_t launch_cv(int cv, const PathArgs& a, int sms, cudaStream_t st, int* blocks) {
+template <class P, class T, int CV, bool MULTI>
+static cudaError_t occupancy_one(int threads, int* occ) {
+  void (*kern)(PathArgs);
+  if constexpr (P::kDim == 3)
+    kern = paths_3d<P, T, CV, MULTI>;
+  else
+    kern = paths_2d<P, T, CV, MULTI>;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, 0);
+}
+
+template <class P, class T, bool MULTI>
+static cudaError_t occupancy_cv(int cv, int threads, int* occ) {
   switch (cv) {
-    case kCvNone: return launch_one<P, T, kCvNone>(a, sms, st, blocks);
-    case kCvGrid: return launch_one<P, T, kCvGrid>(a, sms, st, blocks);
-    default: return launch_one<P, T, kCvExact>(a, sms, st, blocks);
+    case kCvNone: return occupancy_one<P, T, kCvNone, MULTI>(threads, occ);
+    case kCvGrid: return occupancy_one<P, T, kCvGrid, MULTI>(threads, occ);
+    default: return occupancy_one<P, T, kCvExact, MULTI>(threads, occ);
   }
 }
 
-template <class T>
+template <class T, bool MULTI>
+static cudaError_t occupancy_kind(int kind, int cv, int threads, int* occ) {
+  switch (kind) {
+    case 0: return occupancy_cv<Cfg0, T, MULTI>(cv, threads, occ);
+    case 1: return occupancy_cv<Aniso, T, MULTI>(cv, threads, occ);
+    case 2: return occupancy_cv<Cube3, T, MULTI>(cv, threads, occ);
+    default: return occupancy_cv<Harmonic, T, MULTI>(cv, threads, occ);
+  }
+}
+
+cudaError_t occupancy_paths(int kind, int precision, int cv, bool multi, int threads, int* occ) {
+  if (threads % 32 != 0 || threads < 32 || threads > kMaxBlockThreads) return cudaErrorInvalidValue;
+  if (precision == 1)
+    return multi ? occupancy_kind<double, true>(kind, cv, threads, occ)
+                 : occupancy_kind<double, false>(kind, cv, threads, occ);
+  return multi ? occupancy_kind<float, true>(kind, cv, threads, occ)
+               : occupancy_kind<float, false>(kind, cv, threads, occ);
+}
+
+template <class P, class T, bool MULTI>
+static cudaError_t launch_cv(int cv, const PathArgs& a, int sms, cudaStream_t st, int* blocks) {
+  switch (cv) {
+    case kCvNone: return launch_one<P, T, kCvNone, MULTI>(a, sms, st, blocks);
+    case kCvGrid: return launch_one<P, T, kCvGrid, MULTI>(a, sms, st, blocks);
+    default: return launch_one<P, T, kCvExact, MULTI>(a, sms, st, blocks);
+  }
+}
+
+template <class T, bool MULTI>
 static cudaError_t launch_kind(int kind, int cv, const PathArgs& a, int sms, cudaStream_t st,
                                int* blocks) {
   switch (kind) {
-    case 0: return launch_cv<Cfg0, T>(cv, a, sms, st, blocks);
-    case 1: return launch_cv<Aniso, T>(cv, a, sms, st, blocks);
-    case 2: return launch_cv<Cube3, T>(cv, a, sms, st, blocks);
-    default: return launch_cv<Harmonic, T>(cv, a, sms, st, blocks);
+    case 0: return launch_cv<Cfg0, T, MULTI>(cv, a, sms, st, blocks);
+    case 1: return launch_cv<Aniso, T, MULTI>(cv, a, sms, st, blocks);
+    case 2: return launch_cv<Cube3, T, MULTI>(cv, a, sms, st, blocks);
+    default: return launch_cv<Harmonic, T, MULTI>(cv, a, sms, st, blocks);
   }
 }
 
 cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int num_sms,
                          cudaStream_t st, int* blocks) {
-  return precision == 1 ? launch_kind<double>(kind, cv, a, num_sms, st, blocks)
-                        : launch_kind<float>(kind, cv, a, num_sms, st, blocks);
+  if (a.n_segs < 1 || a.n_segs > kMaxSegments) return cudaErrorInvalidValue;
+  const bool multi = a.n_segs > 1;
+  if (precision == 1)
+    return multi ? launch_kind<double, true>(kind, cv, a, num_sms, st, blocks)
+                 : launch_kind<double, false>(kind, cv, a, num_sms, st, blocks);
+  return multi ? launch_kind<float, true>(kind, cv, a, num_sms, st, blocks)
+               : launch_kind<float, false>(kind, cv, a, num_sms, st, blocks);
 }
 
 cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, double kappa,

@@ -29,7 +29,8 @@ PDD_GRID_VALUES, PDD_GRID_GRADIENT = 0, 1
 PDD_DTYPE_F32, PDD_DTYPE_F64 = 0, 1
 PDD_CV_NONE, PDD_CV_EXACT = -1, -2
 PDD_MAX_GRIDS = 8
-PDD_FLAG_EMIT_PATHS, PDD_FLAG_ASYNC = 1, 2
+PDD_FLAG_EMIT_PATHS, PDD_FLAG_ASYNC, PDD_FLAG_GRAPH = 1, 2, 4
+PDD_MAX_LEVELS = 32
 
 STAT_FIELDS = ["mean_phi", "var_phi", "mean_cv", "var_cv", "cov_phi_xi", "var_xi", "rho",
                "se_phi", "se_cv", "vr", "pred_speedup", "mean_steps"]
@@ -83,6 +84,14 @@ _SIGS = [
                                            ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
     ("pdd_ctx_launch_count", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    ("pdd_ctx_graph_count", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    ("pdd_ctx_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("pdd_estimate_levels", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.POINTER(EstimateArgs),
+                                           ctypes.POINTER(NodeStats), ctypes.c_uint32]),
+    ("pdd_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
+                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double)]),
     ("pdd_create_problem", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProblemDesc),
                                           ctypes.POINTER(ctypes.c_void_p)]),
     ("pdd_destroy_problem", ctypes.c_int, [ctypes.c_void_p]),
@@ -165,6 +174,31 @@ def pdd_ctx_launch_count(ctx: int) -> int:
     return n.value
 
 
+def pdd_ctx_graph_count(ctx: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().pdd_ctx_graph_count(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def pdd_ctx_set_launch(ctx: int, block_threads: int, max_blocks: int) -> None:
+    _check(lib().pdd_ctx_set_launch(ctx, block_threads, max_blocks))
+
+
+def pdd_estimate_levels(problem: int, levels, outs, flags: int = 0) -> int:
+    """levels: sequence of EstimateArgs; outs: sequence of NodeStats."""
+    n = len(levels)
+    la = (EstimateArgs * n)(*levels)
+    lo = (NodeStats * n)(*outs)
+    return _check(lib().pdd_estimate_levels(problem, n, la, lo, flags))
+
+
+def pdd_autotune(problem: int, sample: EstimateArgs) -> tuple[int, int, float]:
+    t, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().pdd_autotune(problem, ctypes.byref(sample), ctypes.byref(t), ctypes.byref(b),
+                              ctypes.byref(ms)))
+    return t.value, b.value, ms.value
+
+
 def pdd_create_problem(ctx: int, desc: ProblemDesc) -> int:
     h = ctypes.c_void_p()
     _check(lib().pdd_create_problem(ctx, ctypes.byref(desc), ctypes.byref(h)))
@@ -243,6 +277,12 @@ class Context:
     def launch_count(self) -> int:
         return pdd_ctx_launch_count(self.handle)
 
+    def graph_count(self) -> int:
+        return pdd_ctx_graph_count(self.handle)
+
+    def set_launch(self, block_threads: int = 0, max_blocks: int = 0) -> None:
+        pdd_ctx_set_launch(self.handle, block_threads, max_blocks)
+
     def close(self) -> None:
         if self.handle:
             pdd_ctx_destroy(self.handle)
@@ -282,15 +322,8 @@ class Problem:
                         int(data.is_cuda), data.data_ptr())
         pdd_set_control_grid(self.handle, grid_id, desc)
 
-    def estimate(self, nodes, n_paths: int, dt: float, grid_id: int = PDD_CV_NONE,
-                 seed: int = 1234, stream_tag: int = 0, kappa: float = 1.0,
-                 emit_paths: bool = False, device_out: bool = True, async_: bool = False,
-                 host_inputs: bool = False, pin_host: bool = False):
-        """Estimate every node.  nodes: (n, D) tensor or array of coordinates,
-        or a list of D contiguous float32 columns.  Returns a dict of per-node
-        tensors (and per-path tensors when emit_paths), plus 'status'.
-        host_inputs/device_out choose host or device buffers for the C call;
-        pin_host allocates host outputs in page-locked memory."""
+    def _prepare(self, nodes, n_paths, dt, grid_id, seed, stream_tag, kappa, emit_paths,
+                 device_out, host_inputs, pin_host):
         torch = _torch()
         import numpy as np
         dev = torch.device("cuda", self.ctx.device)
@@ -320,7 +353,7 @@ class Problem:
         args.kappa = kappa
         args.seed = seed
         args.stream_tag = stream_tag
-        args.flags = (PDD_FLAG_EMIT_PATHS if emit_paths else 0) | (PDD_FLAG_ASYNC if async_ else 0)
+        args.flags = PDD_FLAG_EMIT_PATHS if emit_paths else 0
         res = {}
         if emit_paths:
             res["phi"] = torch.empty((n, n_paths), dtype=torch.float32, device=dev)
@@ -340,8 +373,48 @@ class Problem:
             res[f] = torch.empty(n, dtype=torch.int64, device=odev, pin_memory=pin)
             setattr(out, f, res[f].data_ptr())
         res["_keep"] = cols  # inputs must outlive an asynchronous call
+        return args, out, res
+
+    def estimate(self, nodes, n_paths: int, dt: float, grid_id: int = PDD_CV_NONE,
+                 seed: int = 1234, stream_tag: int = 0, kappa: float = 1.0,
+                 emit_paths: bool = False, device_out: bool = True, async_: bool = False,
+                 host_inputs: bool = False, pin_host: bool = False):
+        """Estimate every node.  nodes: (n, D) tensor or array of coordinates,
+        or a list of D contiguous float32 columns.  Returns a dict of per-node
+        tensors (and per-path tensors when emit_paths), plus 'status'.
+        host_inputs/device_out choose host or device buffers for the C call;
+        pin_host allocates host outputs in page-locked memory."""
+        args, out, res = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, kappa,
+                                       emit_paths, device_out, host_inputs, pin_host)
+        if async_:
+            args.flags |= PDD_FLAG_ASYNC
         res["status"] = pdd_estimate_nodes(self.handle, args, out)
         return res
+
+    def estimate_levels(self, levels, async_: bool = False, graph: bool = False,
+                        device_out: bool = True, host_inputs: bool = False):
+        """Several levels in one launch.  levels: list of dicts with the
+        keyword arguments of estimate() (nodes, n_paths, dt, grid_id, seed,
+        stream_tag, kappa, emit_paths).  Returns (status, [per-level dict])."""
+        prepared = []
+        for lv in levels:
+            prepared.append(self._prepare(lv["nodes"], lv["n_paths"], lv["dt"],
+                                          lv.get("grid_id", PDD_CV_NONE), lv.get("seed", 1234),
+                                          lv.get("stream_tag", 0), lv.get("kappa", 1.0),
+                                          lv.get("emit_paths", False), device_out, host_inputs,
+                                          False))
+        flags = (PDD_FLAG_ASYNC if async_ else 0) | (PDD_FLAG_GRAPH if graph else 0)
+        st = pdd_estimate_levels(self.handle, [p[0] for p in prepared], [p[1] for p in prepared],
+                                 flags)
+        return st, [p[2] for p in prepared]
+
+    def autotune(self, nodes, n_paths: int, dt: float, grid_id: int = PDD_CV_NONE,
+                 seed: int = 1234, stream_tag: int = 0):
+        """Pick the fastest launch shape for this kind of call; returns
+        (block_threads, max_blocks, ms)."""
+        args, _, keep = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, 1.0, False,
+                                      True, False, False)
+        return pdd_autotune(self.handle, args)
 
     def estimate_on_stream(self, *a, **kw):
         """estimate() with the output tensors allocated on the context's
