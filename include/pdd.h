@@ -242,6 +242,57 @@ int pdd_estimate_levels(pdd_problem* problem, int n_levels, const pdd_estimate_a
 int pdd_autotune(pdd_problem* problem, const pdd_estimate_args* sample, int* best_threads,
                  int* best_max_blocks, double* best_ms);
 
+/* ---- Serving: continuous batching of estimate requests -------------------
+   A server admits requests (one pdd_estimate_args each: nodes, n_paths, dt,
+   grid, seed, stream_tag) while a slot of the running batch and room in its
+   device arena are free, and runs the admitted requests together: every
+   scheduler iteration is one persistent launch that carries a slice of paths
+   from each of up to max_active requests (requests of the same problem and
+   control-variate class share a launch), so requests arriving while others
+   run join the next launch.  Results are bit-identical to pdd_estimate_nodes
+   on the same arguments (exact sums keyed by node and path).  A scheduler
+   thread owned by the server issues launches on two streams of its own and
+   polls CUDA events; nothing on the device waits.                          */
+typedef struct {
+  int32_t max_active;          /* requests in the running batch, 1..32 (0: 32) */
+  int32_t max_queue;           /* pending requests before PDD_ERR_BUSY (0: 256) */
+  int64_t quantum_path_steps;  /* target path-steps per launch (0: 8e9) */
+  size_t device_arena_bytes;   /* device memory for admitted requests (0: 256 MiB);
+                                  a request takes about 252 B per node */
+} pdd_server_desc;
+
+typedef struct {
+  int64_t submitted, admitted, rejected_busy, rejected_invalid, rejected_nomem;
+  int64_t completed, cancelled, failed, launches, pending, active;
+} pdd_server_stats;
+
+int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** out);
+/* Copies the request (coordinates from host or device memory, read before the
+   call returns) and queues it; never waits for the GPU.  PDD_ERR_BUSY when
+   max_queue requests are pending (retry or shed), PDD_ERR_NOMEM when the
+   request can never fit the arena, PDD_ERR_INVALID for malformed requests
+   (EMIT_PATHS is not served).  *ticket identifies the request.             */
+int pdd_submit(pdd_server* server, pdd_problem* problem, const pdd_estimate_args* args,
+               uint64_t* ticket);
+/* Waits up to timeout_us (0: do not wait) for the request.  PDD_OK: results
+   copied into *out (host or device per out->on_device) and the ticket is
+   released; PDD_ERR_NOT_READY / PDD_ERR_TIMEOUT: still running (ticket kept);
+   PDD_ERR_CANCELLED: cancelled (ticket released); other errors: the request
+   failed (ticket released).                                                 */
+int pdd_poll(pdd_server* server, uint64_t ticket, pdd_node_stats* out, int timeout_us);
+/* Stops issuing the request's paths; its memory is released once no launch
+   in flight uses it; pdd_poll then returns PDD_ERR_CANCELLED.               */
+int pdd_cancel(pdd_server* server, uint64_t ticket);
+int pdd_server_get_stats(pdd_server* server, pdd_server_stats* out);
+/* Test hook, host side only: 1 = the next admission fails as if the arena
+   allocation failed (that request ends with PDD_ERR_NOMEM); 2 = the next
+   scheduled request is dropped as if the worker running it died (it ends
+   with PDD_ERR_CANCELLED).  Other requests are unaffected.                 */
+int pdd_server_inject_fault(pdd_server* server, int fault);
+/* Cancels queued and running requests, waits for launches in flight (they
+   end by themselves) and frees the server.                                  */
+void pdd_server_destroy(pdd_server* server);
+
 /* ---- Allocation-free estimate (the paper has no counterpart) -------------
    The same estimate as pdd_estimate_nodes, for callers that cannot let the
    library allocate device memory: for example an application whose own pool

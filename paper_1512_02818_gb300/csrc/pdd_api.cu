@@ -105,6 +105,19 @@ struct WsHeader {
 };
 
 namespace pdd {
+// Device, SM count and launch shape of a context, for the serving runtime.
+bool ctx_view(pdd_ctx* c, int* device, int* num_sms, int* block_threads, int* max_blocks) {
+  if (!c) return false;
+  *device = c->device;
+  *num_sms = c->num_sms;
+  *block_threads = c->block_threads;
+  *max_blocks = c->max_blocks;
+  return true;
+}
+pdd_ctx* problem_ctx(pdd_problem* p) { return p ? p->ctx : nullptr; }
+}  // namespace pdd
+
+namespace pdd {
 // Read-only view of a problem and its context for other translation units of
 // the library (the allocation-free entry point).
 bool problem_view(pdd_problem* p, ProblemView* v) {
@@ -307,7 +320,6 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
                    [&](int x, int y) { return levels[x].dt < levels[y].dt; });
   PathArgs pa{};
   pa.cursor = &hdr->cursor;
-  pa.acc = acc;
   pa.err = &hdr->err;
   pa.trunc_total = &hdr->trunc_total;
   pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
@@ -343,6 +355,9 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
     sg.begin = begin;
     sg.total = (unsigned long long)a.n_nodes * (unsigned long long)a.n_paths;
     sg.n_paths = (unsigned long long)a.n_paths;
+    sg.acc = acc + (size_t)rec_base[l] * kAccWords;
+    sg.path_off = 0;
+    sg.emit_stride = (unsigned long long)a.n_paths;
     sg.grad = plan[l].table;
     const bool emit = (a.flags & PDD_FLAG_EMIT_PATHS) != 0;
     sg.emit_phi = emit ? a.path_phi : nullptr;
@@ -351,7 +366,6 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
     sg.h = a.dt;
     sg.sqrt_h = std::sqrt(a.dt);
     sg.thr0 = c0 * sg.sqrt_h;
-    sg.rec_base = rec_base[l];
     sg.key0 = (uint32_t)a.seed;
     sg.key1 = a.stream_tag;
     sg.seed_hi = (uint32_t)(a.seed >> 32);

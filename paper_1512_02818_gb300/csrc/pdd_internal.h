@@ -19,21 +19,25 @@ constexpr int kMaxSegments = 32;           // segments (levels / requests) per l
 
 // One segment of a launch: n_nodes x n_paths paths with their own nodes,
 // time step, control grid, random-stream key and output records.
+// The segment covers paths path_off .. path_off + n_paths - 1 of each of its
+// n_nodes nodes (a slice of a request when a request is spread over launches).
 struct SegArgs {
   const float* cx;
   const float* cy;
   const float* cz;
   unsigned long long begin;    // first index of the segment in the launch's flat path space
   unsigned long long total;    // n_nodes * n_paths
-  unsigned long long n_paths;
+  unsigned long long n_paths;  // paths per node in this segment
+  unsigned long long* acc;     // node records of the segment's nodes (16 words each)
   const void* grad;            // float2 (2D) / float4 (3D) gradient table; null: no grid
-  float* emit_phi;             // optional per-path outputs (node-major within the segment)
+  float* emit_phi;             // optional per-path outputs: [node * emit_stride + path]
   float* emit_xi;
   int* emit_steps;
+  unsigned long long emit_stride;
   double h;
   double sqrt_h;
   double thr0;                 // c0 sqrt(h)
-  uint32_t rec_base;           // first node record of the segment
+  uint32_t path_off;           // first path index of the segment
   uint32_t key0, key1, seed_hi;
   int grid_n;
   int max_steps;
@@ -43,7 +47,6 @@ struct SegArgs {
 struct PathArgs {
   unsigned long long total;    // sum of the segments' totals
   unsigned long long* cursor;  // flat path cursor, zeroed before the launch
-  unsigned long long* acc;     // node records (16 words of exact sums each), zeroed
   unsigned* err;               // error bits (kErr*)
   unsigned long long* trunc_total;
   int y_exp;
@@ -86,6 +89,8 @@ struct ProblemView {
 
 static_assert(PDD_MAX_GRIDS == 8, "ProblemView holds 8 grid slots");
 bool problem_view(pdd_problem* p, ProblemView* v);
+bool ctx_view(pdd_ctx* c, int* device, int* num_sms, int* block_threads, int* max_blocks);
+pdd_ctx* problem_ctx(pdd_problem* p);
 
 cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int num_sms,
                          cudaStream_t st, int* blocks);

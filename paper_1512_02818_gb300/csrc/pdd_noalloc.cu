@@ -154,7 +154,6 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   PathArgs pa{};
   pa.total = (unsigned long long)n * (unsigned long long)a->n_paths;
   pa.cursor = &hdr->cursor;
-  pa.acc = acc;
   pa.err = &hdr->err;
   pa.trunc_total = &hdr->trunc_total;
   pa.y_exp = pv.y_rule == PDD_Y_EXP;
@@ -168,6 +167,9 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   sg.begin = 0;
   sg.total = pa.total;
   sg.n_paths = (unsigned long long)a->n_paths;
+  sg.acc = acc;
+  sg.path_off = 0;
+  sg.emit_stride = (unsigned long long)a->n_paths;
   sg.grad = table;
   sg.emit_phi = emit ? a->path_phi : nullptr;
   sg.emit_xi = emit ? a->path_xi : nullptr;
@@ -176,7 +178,6 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   sg.sqrt_h = std::sqrt(a->dt);
   const double c0 = pv.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
   sg.thr0 = c0 * sg.sqrt_h;
-  sg.rec_base = 0;
   sg.key0 = (uint32_t)a->seed;
   sg.key1 = a->stream_tag;
   sg.seed_hi = (uint32_t)(a->seed >> 32);

@@ -74,10 +74,10 @@ __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long
   if (sg.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
     const uint32_t gg = (uint32_t)li, np = (uint32_t)sg.n_paths;
     s.node = gg / np;
-    s.path = gg - s.node * np;
+    s.path = sg.path_off + (gg - s.node * np);
   } else {
     s.node = (uint32_t)(li / sg.n_paths);
-    s.path = (uint32_t)(li - (unsigned long long)s.node * sg.n_paths);
+    s.path = sg.path_off + (uint32_t)(li - (unsigned long long)s.node * sg.n_paths);
   }
   s.seg = si;
   s.x[0] = (T)__ldg(sg.cx + s.node);
@@ -164,7 +164,7 @@ __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T
   const bool ok = to_fixed(phi, qa) & to_fixed(psi, qb);
   if (!ok) atomicOr(a.err, kErrOverflow);
   const SegArgs& sg = a.seg[MULTI ? s.seg : 0];
-  unsigned long long* w = a.acc + (size_t)(sg.rec_base + s.node) * kAccWords;
+  unsigned long long* w = sg.acc + (size_t)s.node * kAccWords;
   atomic_add_s64(w + 0, qa);
   atomic_add_prod(w + 2, qa, qa);
   atomic_add_s64(w + 4, qb);
@@ -179,7 +179,7 @@ __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T
     atomicAdd(a.trunc_total, 1ull);
   }
   if (sg.emit_phi != nullptr) {
-    const size_t i = (size_t)s.node * sg.n_paths + s.path;
+    const size_t i = (size_t)s.node * sg.emit_stride + s.path;
     sg.emit_phi[i] = (float)phi;
     sg.emit_xi[i] = (float)xi;
     sg.emit_steps[i] = s.k;

@@ -68,6 +68,20 @@ class NodeStats(ctypes.Structure):
                 + [(f, ctypes.c_void_p) for f in STAT_FIELDS + COUNT_FIELDS])
 
 
+class ServerDesc(ctypes.Structure):
+    _fields_ = [("max_active", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("quantum_path_steps", ctypes.c_int64), ("device_arena_bytes", ctypes.c_size_t)]
+
+
+SERVER_STAT_FIELDS = ["submitted", "admitted", "rejected_busy", "rejected_invalid",
+                      "rejected_nomem", "completed", "cancelled", "failed", "launches", "pending",
+                      "active"]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in SERVER_STAT_FIELDS]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -99,6 +113,16 @@ _SIGS = [
                                             ctypes.POINTER(GridDesc)]),
     ("pdd_estimate_nodes", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
                                           ctypes.POINTER(NodeStats)]),
+    ("pdd_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerDesc),
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    ("pdd_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
+                                  ctypes.POINTER(ctypes.c_uint64)]),
+    ("pdd_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(NodeStats),
+                                ctypes.c_int]),
+    ("pdd_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("pdd_server_get_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerStats)]),
+    ("pdd_server_inject_fault", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("pdd_server_destroy", None, [ctypes.c_void_p]),
     ("pdd_estimate_nodes_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
                                                   ctypes.POINTER(NodeStats)]),
     ("pdd_debug_philox", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -219,6 +243,43 @@ def pdd_estimate_nodes(problem: int, args: EstimateArgs, out: NodeStats) -> int:
 
 
 PDD_NOALLOC_MAX_NODES = 4096
+
+
+def pdd_server_create(ctx: int, desc: ServerDesc | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().pdd_server_create(ctx, ctypes.byref(desc) if desc is not None else None,
+                                   ctypes.byref(h)))
+    return h.value
+
+
+def pdd_submit(server: int, problem: int, args: EstimateArgs) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().pdd_submit(server, problem, ctypes.byref(args), ctypes.byref(t)))
+    return t.value
+
+
+def pdd_poll(server: int, ticket: int, out: NodeStats, timeout_us: int) -> int:
+    """Returns the raw status (PDD_OK, PDD_ERR_NOT_READY, PDD_ERR_TIMEOUT,
+    PDD_ERR_CANCELLED or another error) without raising."""
+    return lib().pdd_poll(server, ticket, ctypes.byref(out), timeout_us)
+
+
+def pdd_cancel(server: int, ticket: int) -> None:
+    _check(lib().pdd_cancel(server, ticket))
+
+
+def pdd_server_get_stats(server: int) -> dict:
+    st = ServerStats()
+    _check(lib().pdd_server_get_stats(server, ctypes.byref(st)))
+    return {f: getattr(st, f) for f in SERVER_STAT_FIELDS}
+
+
+def pdd_server_inject_fault(server: int, fault: int) -> None:
+    _check(lib().pdd_server_inject_fault(server, fault))
+
+
+def pdd_server_destroy(server: int) -> None:
+    lib().pdd_server_destroy(server)
 
 
 def pdd_estimate_nodes_noalloc(problem: int, args: EstimateArgs, out: NodeStats) -> int:
@@ -427,6 +488,71 @@ class Problem:
     def close(self) -> None:
         if self.handle:
             pdd_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server on a context (see pdd_server_create)."""
+
+    def __init__(self, ctx: Context, max_active: int = 0, max_queue: int = 0,
+                 quantum_path_steps: int = 0, device_arena_bytes: int = 0):
+        self.ctx = ctx
+        self.handle = pdd_server_create(ctx.handle, ServerDesc(max_active, max_queue,
+                                                               quantum_path_steps,
+                                                               device_arena_bytes))
+
+    def submit(self, problem: Problem, nodes, n_paths: int, dt: float,
+               grid_id: int = PDD_CV_NONE, seed: int = 1234, stream_tag: int = 0,
+               kappa: float = 1.0, flags: int = 0) -> int:
+        """nodes: (n, D) numpy array (host); the library copies it."""
+        import numpy as np
+        nodes = np.asarray(nodes, dtype=np.float32).reshape(-1, problem.dim)
+        cols = [np.ascontiguousarray(nodes[:, j]) for j in range(problem.dim)]
+        a = EstimateArgs()
+        a.n_nodes = nodes.shape[0]
+        for j in range(3):
+            a.coords[j] = cols[j].ctypes.data if j < problem.dim else None
+        a.coords_on_device = 0
+        a.grid_id = grid_id
+        a.n_paths = n_paths
+        a.dt = dt
+        a.kappa = kappa
+        a.seed = seed
+        a.stream_tag = stream_tag
+        a.flags = flags
+        return pdd_submit(self.handle, problem.handle, a)
+
+    def poll(self, ticket: int, n_nodes: int, timeout_us: int = 0):
+        """(status, results) -- results is a dict of numpy arrays when status
+        is PDD_OK, else None."""
+        import numpy as np
+        res = {f: np.empty(n_nodes) for f in STAT_FIELDS}
+        res.update({f: np.empty(n_nodes, dtype=np.int64) for f in COUNT_FIELDS})
+        out = NodeStats()
+        out.on_device = 0
+        for f in STAT_FIELDS + COUNT_FIELDS:
+            setattr(out, f, res[f].ctypes.data if n_nodes else None)
+        st = pdd_poll(self.handle, ticket, out, timeout_us)
+        return st, (res if st == PDD_OK else None)
+
+    def cancel(self, ticket: int) -> None:
+        pdd_cancel(self.handle, ticket)
+
+    def stats(self) -> dict:
+        return pdd_server_get_stats(self.handle)
+
+    def inject_fault(self, fault: int) -> None:
+        pdd_server_inject_fault(self.handle, fault)
+
+    def close(self) -> None:
+        if self.handle:
+            pdd_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,174 @@
+"""Serving (continuous batching) through the C ABI.
+
+Requests of different sizes, path counts, time steps and control grids are
+submitted together; each result must equal, bit for bit, the same request run
+alone with pdd_estimate_nodes (exact sums keyed by node and path).  Admission
+control, cancellation and host-side fault injection must leave the other
+requests' results unchanged.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1512_02818_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1512_02818_gb300 import build, pdd
+    build.build()
+    ctx = pdd.Context(0)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    prob.set_control_grid(0, W.control_grid(0, 129, 1e-1))
+    prob.set_control_grid(1, W.control_grid(0, 129, 1e-2))
+    yield torch, pdd, ctx, prob
+    prob.close()
+    ctx.close()
+
+
+def _requests(seed=3, count=12):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(1, 200))
+        out.append(dict(nodes=W.random_interface_nodes(rng, n), n_paths=int(rng.integers(50, 3000)),
+                        dt=float(rng.choice([1e-2, 1e-3, 2e-4])),
+                        grid_id=int(rng.choice([-1, 0, 1])), stream_tag=100 + i,
+                        seed=1234 + (i % 3)))
+    return out
+
+
+def _alone(prob, r):
+    res = prob.estimate(r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"], seed=r["seed"],
+                        stream_tag=r["stream_tag"])
+    return {k: v.cpu().numpy() for k, v in res.items() if hasattr(v, "cpu")}
+
+
+def _same(pdd, a, b):
+    for f in pdd.STAT_FIELDS + pdd.COUNT_FIELDS:
+        assert np.array_equal(a[f], b[f], equal_nan=True), f
+
+
+def _wait(srv, t, n, timeout_s=120):
+    st, res = srv.poll(t, n, int(timeout_s * 1e6))
+    return st, res
+
+
+def test_mix_equals_alone(env):
+    torch, pdd, ctx, prob = env
+    reqs = _requests()
+    srv = pdd.Server(ctx, max_active=8, quantum_path_steps=20_000_000)
+    tickets = [srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"],
+                          seed=r["seed"], stream_tag=r["stream_tag"]) for r in reqs]
+    for r, t in zip(reqs, tickets):
+        st, res = _wait(srv, t, len(r["nodes"]))
+        assert st == pdd.PDD_OK, pdd.pdd_last_error()
+        _same(pdd, res, _alone(prob, r))
+    s = srv.stats()
+    assert s["completed"] == len(reqs) and s["admitted"] == len(reqs)
+    assert s["launches"] > len(reqs) // 8  # requests were spread over several launches
+    srv.close()
+
+
+def test_arrivals_while_running(env):
+    torch, pdd, ctx, prob = env
+    srv = pdd.Server(ctx, max_active=4, quantum_path_steps=5_000_000)
+    big = dict(nodes=W.workload_nodes("c1")[::4], n_paths=4000, dt=2e-4, grid_id=1,
+               stream_tag=7, seed=5)
+    tb = srv.submit(prob, big["nodes"], big["n_paths"], big["dt"], grid_id=1, seed=5,
+                    stream_tag=7)
+    st, _ = srv.poll(tb, len(big["nodes"]), 0)
+    assert st == pdd.PDD_ERR_NOT_READY
+    small = _requests(seed=9, count=6)
+    ts = []
+    for r in small:  # arrive while the big request runs
+        time.sleep(0.005)
+        ts.append(srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"],
+                             seed=r["seed"], stream_tag=r["stream_tag"]))
+    for r, t in zip(small, ts):
+        st, res = _wait(srv, t, len(r["nodes"]))
+        assert st == pdd.PDD_OK
+        _same(pdd, res, _alone(prob, r))
+    st, res = _wait(srv, tb, len(big["nodes"]))
+    assert st == pdd.PDD_OK
+    _same(pdd, res, _alone(prob, big))
+    srv.close()
+
+
+def test_admission_cancel_and_faults(env):
+    torch, pdd, ctx, prob = env
+    reqs = _requests(seed=21, count=6)
+    # a tiny arena: requests queue for memory; a request larger than it is refused
+    srv = pdd.Server(ctx, max_active=2, max_queue=3, quantum_path_steps=10_000_000,
+                     device_arena_bytes=200 * 256 * 2)
+    with pytest.raises(pdd.PddError) as e:
+        srv.submit(prob, W.workload_nodes("c4")[:4000], 10, 1e-3)
+    assert e.value.status == pdd.PDD_ERR_NOMEM
+    with pytest.raises(pdd.PddError) as e:
+        srv.submit(prob, reqs[0]["nodes"], 10, 1e-3, flags=pdd.PDD_FLAG_EMIT_PATHS)
+    assert e.value.status == pdd.PDD_ERR_INVALID
+    with pytest.raises(pdd.PddError):
+        srv.submit(prob, reqs[0]["nodes"], 10, 1e-3, grid_id=6)
+    srv.close()
+
+    srv = pdd.Server(ctx, max_active=2, max_queue=4, quantum_path_steps=10_000_000)
+    long_req = dict(nodes=W.workload_nodes("c1"), n_paths=200_000, dt=1e-4, grid_id=1,
+                    stream_tag=1, seed=1)
+    t_long = srv.submit(prob, long_req["nodes"], long_req["n_paths"], 1e-4, grid_id=1)
+    deadline = time.time() + 30
+    while srv.stats()["admitted"] < 1 and time.time() < deadline:
+        time.sleep(0.001)
+    srv.inject_fault(1)  # the next admission fails
+    t_fail = srv.submit(prob, reqs[0]["nodes"], reqs[0]["n_paths"], reqs[0]["dt"])
+    tickets = []
+    busy = 0
+    for r in reqs[1:]:
+        try:
+            tickets.append((r, srv.submit(prob, r["nodes"], r["n_paths"], r["dt"],
+                                          grid_id=r["grid_id"], seed=r["seed"],
+                                          stream_tag=r["stream_tag"])))
+        except pdd.PddError as ex:
+            assert ex.status == pdd.PDD_ERR_BUSY
+            busy += 1
+    srv.cancel(t_long)
+    st, _ = _wait(srv, t_long, len(long_req["nodes"]))
+    assert st == pdd.PDD_ERR_CANCELLED
+    st, _ = _wait(srv, t_fail, len(reqs[0]["nodes"]))
+    assert st == pdd.PDD_ERR_NOMEM
+    for r, t in tickets:
+        st, res = _wait(srv, t, len(r["nodes"]))
+        assert st == pdd.PDD_OK
+        _same(pdd, res, _alone(prob, r))
+    s = srv.stats()
+    assert s["rejected_busy"] == busy and s["cancelled"] == 1 and s["failed"] == 1
+    # a request dropped mid-flight (its worker lost) leaves the others intact
+    srv.inject_fault(2)
+    more = _requests(seed=33, count=3)
+    tk = [srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"],
+                     seed=r["seed"], stream_tag=r["stream_tag"]) for r in more]
+    statuses = []
+    for r, t in zip(more, tk):
+        st, res = _wait(srv, t, len(r["nodes"]))
+        statuses.append(st)
+        if st == pdd.PDD_OK:
+            _same(pdd, res, _alone(prob, r))
+    assert statuses.count(pdd.PDD_ERR_CANCELLED) == 1
+    assert statuses.count(pdd.PDD_OK) == len(more) - 1
+    with pytest.raises(pdd.PddError):
+        srv.cancel(123456789)
+    srv.close()
+
+
+def test_destroy_with_work_in_flight(env):
+    torch, pdd, ctx, prob = env
+    srv = pdd.Server(ctx, max_active=2, quantum_path_steps=5_000_000)
+    for r in _requests(seed=44, count=5):
+        srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"])
+    srv.close()  # cancels and waits for the launches in flight; must return
+    torch.cuda.synchronize()
