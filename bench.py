@@ -67,6 +67,12 @@ def parse_args():
     ap.add_argument("--cpu-paths", type=int, default=1000)
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 64 of the 256 nodes x 2e4 paths (same kernels)")
+    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c1",
+                    help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c2: 3D "
+                         "three-level cascade in one launch (CUDA graph); c3: serving with "
+                         "Poisson arrivals; c4: anisotropic 2D, FP32 vs FP64 paths")
+    ap.add_argument("--window", type=float, default=10.0, help="c3: arrival window (s)")
+    ap.add_argument("--rate", type=float, default=200.0, help="c3: arrivals per second")
     return ap.parse_args()
 
 
@@ -155,6 +161,16 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers ---
+def smi_id(local: int) -> str:
+    """nvidia-smi -i selector of the CUDA device `local` (its UUID)."""
+    import torch
+    uuid = getattr(torch.cuda.get_device_properties(local), "uuid", None)
+    if uuid is None:
+        return str(local)
+    u = str(uuid)
+    return u if u.startswith("GPU-") else "GPU-" + u
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -207,9 +223,7 @@ def run_ours(args, rank, world, local):
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
-    uuid = getattr(props, "uuid", None)
-    gpu_id = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else (
-        str(uuid) if uuid is not None else str(local))
+    gpu_id = smi_id(local)
 
     # CPU baseline pool first (spawned workers, rank 0 at N=1 only)
     cpu_baseline = None
@@ -401,9 +415,286 @@ def run_reference(args):
     }
 
 
+# ----------------------------------------------------------- other workloads ---
+def _timed_steps(torch, stream, steps, fn, flush):
+    """CUDA-event times (ms) of `steps` calls of fn() on `stream`, L2 flushed between."""
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def run_c2(args):
+    """3D cube, 4^3 subdomains, 9,216 nodes; three levels (1e3/1e4/1e5 paths at
+    dt 1e-2/1e-3/1e-4 with eps 1e-1/1e-2/1e-3 grids on 65^3) plus a plain pass
+    at the coarsest level, all in one persistent launch replayed from a CUDA
+    graph."""
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    ctx = pdd.Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CUBE_3D)
+    levels_cfg = W.WORKLOADS["c2"]["levels"]
+    for slot, lv in enumerate(levels_cfg):
+        prob.set_control_grid(slot, W.control_grid(2, 65, lv["eps"]))
+    nodes = W.workload_nodes("c2")
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).to(dev) for j in range(3)]
+    lv = [dict(nodes=cols, n_paths=c["n_paths"], dt=c["dt"], grid_id=i, stream_tag=1 + i)
+          for i, c in enumerate(levels_cfg)]
+    lv.append(dict(nodes=cols, n_paths=levels_cfg[0]["n_paths"], dt=levels_cfg[0]["dt"],
+                   grid_id=pdd.PDD_CV_NONE, stream_tag=1))
+    prepared = [prob._prepare(l["nodes"], l["n_paths"], l["dt"], l["grid_id"], SEED,
+                              l["stream_tag"], 1.0, False, True, False, False) for l in lv]
+    largs, louts = [p[0] for p in prepared], [p[1] for p in prepared]
+
+    def step():
+        pdd.pdd_estimate_levels(prob.handle, largs, louts, pdd.PDD_FLAG_GRAPH | pdd.PDD_FLAG_ASYNC)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    clocks = ClockSampler(smi_id(0))
+    ms = _timed_steps(torch, ctx.stream, args.steps, step, flush)
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    res = [{k: v.cpu().numpy() for k, v in p[2].items() if torch.is_tensor(v)} for p in prepared]
+    u = W.exact_u(2, nodes.astype(np.float64))
+    per_level = []
+    work = 0.0
+    for i, r in enumerate(res):
+        steps_l = float((r["mean_steps"] * r["n_paths"]).sum())
+        work += steps_l
+        mean = r["mean_cv"] if i < 3 else r["mean_phi"]
+        per_level.append({"n_paths": lv[i]["n_paths"], "dt": lv[i]["dt"],
+                          "cv": "grid eps %g" % levels_cfg[i]["eps"] if i < 3 else "plain",
+                          "path_steps": steps_l,
+                          "rmse": float(np.sqrt(np.mean((mean - u) ** 2))),
+                          "median_vr": float(np.nanmedian(r["vr"])) if i < 3 else 1.0,
+                          "mean_steps": float(np.mean(r["mean_steps"]))})
+    total_ms = sum(ms)
+    value = work * args.steps / (total_ms / 1e3)
+    line = {"workload": "c2", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "3D cube b=0 c=1 u=e^x sin y cos z + xyz, 4^3 subdomains, "
+                                   "9216 nodes, levels (1e3,1e-2,eps 1e-1) (1e4,1e-3,eps 1e-2) "
+                                   "(1e5,1e-4,eps 1e-3) on 65^3 grids + plain level-1 pass, one "
+                                   "persistent launch replayed from a CUDA graph",
+                       "l2": "flushed between steps (256 MB)"},
+            "nodes_per_s": len(nodes) * args.steps / (total_ms / 1e3),
+            "levels": per_level, "graph_captures": ctx.graph_count(),
+            "gpu_launches": int(launches), "clocks": clk,
+            "roofline": {"bound": "alu", "unit": "T thread-instr/s",
+                         "achieved": 190.0 * value / 1e12,
+                         "peak": torch.cuda.get_device_properties(0).multi_processor_count
+                         * 4 * 32 * 2.070e9 / 1e12,
+                         "algorithmic": "190 thread-instr per 3D control-variate path-step"}}
+    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    prob.close()
+    ctx.close()
+    return line
+
+
+def run_c3(args):
+    """Serving: Poisson arrivals of requests over the 2D problem (1-4,096 nodes
+    log-uniform, 1e3-1e6 paths log-uniform, dt in {1e-2,1e-3,1e-4}, eps in
+    {none, 1e-1, 1e-2}); continuous batching; p50/p99 latency of completed
+    requests.  Runs the offered rate, then 0.7x the measured capacity."""
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    ctx = pdd.Context(0)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    prob.set_control_grid(0, W.control_grid(0, GRID_N, 1e-1))
+    prob.set_control_grid(1, W.control_grid(0, GRID_N, 1e-2))
+    gid = {None: pdd.PDD_CV_NONE, 1e-1: 0, 1e-2: 1}
+
+    def serve(rate, window, drain_s, seed):
+        reqs = W.serving_requests(seed, rate, window)
+        srv = pdd.Server(ctx, max_active=32, max_queue=64, device_arena_bytes=1 << 30)
+        t0 = time.perf_counter()
+        outstanding, lat, done_steps, done_nodes, rejected = {}, [], 0.0, 0, 0
+        i = 0
+
+        def poll_all():
+            nonlocal done_steps, done_nodes
+            for t in list(outstanding):
+                r = outstanding[t]
+                st, res = srv.poll(t, r["n_nodes"], 0)
+                if st == pdd.PDD_ERR_NOT_READY:
+                    continue
+                del outstanding[t]
+                if st == pdd.PDD_OK:
+                    lat.append(time.perf_counter() - t0 - r["arrival"])
+                    done_steps += float((res["mean_steps"] * res["n_paths"]).sum())
+                    done_nodes += r["n_nodes"]
+
+        while i < len(reqs) or (outstanding and time.perf_counter() - t0 < window + drain_s):
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i]["arrival"] <= now:
+                r = reqs[i]
+                i += 1
+                try:
+                    t = srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=gid[r["eps"]],
+                                   seed=SEED, stream_tag=r["tag"])
+                    outstanding[t] = r
+                except pdd.PddError:
+                    rejected += 1
+            poll_all()
+            time.sleep(0.001)
+        elapsed = time.perf_counter() - t0
+        unfinished = len(outstanding)
+        for t in list(outstanding):
+            srv.cancel(t)
+        stats = srv.stats()
+        srv.close()
+        offered = sum(float(r["n_nodes"]) * r["n_paths"] * 0.12 / r["dt"] for r in reqs)
+        return {"rate_per_s": rate, "window_s": window, "offered_requests": len(reqs),
+                "offered_path_steps_per_s_est": offered / window,
+                "completed": len(lat), "rejected_busy": rejected,
+                "cancelled_at_end": unfinished, "launches": stats["launches"],
+                "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat else None,
+                "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat else None,
+                "completed_path_steps_per_s": done_steps / elapsed,
+                "completed_nodes_per_s": done_nodes / elapsed, "elapsed_s": elapsed}
+
+    clocks = ClockSampler(smi_id(0))
+    # capacity: one large request (256 nodes x 1e5 paths, dt 1e-4, eps 1e-2) alone
+    # through the server gives its sustained path-steps/s
+    srv = pdd.Server(ctx, max_active=32, max_queue=64, device_arena_bytes=1 << 30)
+    cal_nodes = W.workload_nodes("c1")
+    tc = time.perf_counter()
+    t = srv.submit(prob, cal_nodes, N_PATHS, DT, grid_id=1, seed=SEED, stream_tag=999)
+    st, res = srv.poll(t, len(cal_nodes), int(600e6))
+    cal_s = time.perf_counter() - tc
+    srv.close()
+    cal_rate = float((res["mean_steps"] * res["n_paths"]).sum()) / cal_s
+    sat = serve(args.rate, args.window, 30.0, 11)
+    # capacity in requests/s: sustained rate over the mean offered request size
+    reqs = W.serving_requests(11, args.rate, args.window)
+    mean_req = np.mean([r["n_nodes"] * r["n_paths"] * 0.12 / r["dt"] for r in reqs])
+    cap = cal_rate / mean_req
+    steady = serve(0.7 * cap, max(30.0, args.window), 90.0, 12)
+    clk = clocks.stop()
+    prob.close()
+    ctx.close()
+    return {"workload": "c3", "metric": METRIC, "value": sat["completed_path_steps_per_s"],
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "serving, Poisson arrivals over the 2D CFG0 problem; "
+                                   "1-4096 nodes, 1e3-1e6 paths (log-uniform), dt in "
+                                   "{1e-2,1e-3,1e-4}, eps in {none,1e-1,1e-2}; max_active 32, "
+                                   "max_queue 64, quantum 8e9 path-steps"},
+            "saturation": sat, "at_0.7x_capacity": steady,
+            "served_rate_one_request_path_steps_per_s": cal_rate,
+            "mean_request_path_steps_est": float(mean_req),
+            "capacity_requests_per_s_est": cap, "clocks": clk}
+
+
+def run_c4(args):
+    """Anisotropic 2D, 32x32 subdomains, 31,744 nodes x 1e4 paths, dt = 1e-4,
+    eps = 1e-2 grid on 513^2: FP32 paths at full size; FP32 and FP64 paths on a
+    256-node subsample against the FP64 oracle (first 32 paths of every node)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    ctx = pdd.Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    v = W.control_grid(1, 513, 1e-2)
+    p32 = pdd.Problem(ctx, pdd.PDD_PROBLEM_ANISO_2D)
+    p64 = pdd.Problem(ctx, pdd.PDD_PROBLEM_ANISO_2D, precision=pdd.PDD_PATH_FP64)
+    p32.set_control_grid(0, v)
+    p64.set_control_grid(0, v)
+    nodes = W.workload_nodes("c4")
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).to(dev) for j in range(2)]
+    n_paths, h = 10_000, 1e-4
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    holder = {}
+
+    def full():
+        holder["r"] = p32.estimate(cols, n_paths, h, grid_id=0, async_=True)
+
+    full()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(smi_id(0))
+    ms = _timed_steps(torch, ctx.stream, max(1, args.steps), full, flush)
+    r = {k: t.cpu().numpy() for k, t in holder["r"].items() if torch.is_tensor(t)}
+    work = float((r["mean_steps"] * r["n_paths"]).sum())
+    sub = nodes[::124][:256]
+    res, tms = {}, {}
+    for name, prob in (("fp32", p32), ("fp64", p64)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        rr = prob.estimate(sub, n_paths, h, grid_id=0, emit_paths=True)
+        e1.record(ctx.stream)
+        ctx.stream.synchronize()
+        tms[name] = e0.elapsed_time(e1)
+        res[name] = rr
+    clk = clocks.stop()
+    k = 32
+    ni = np.repeat(np.arange(len(sub)), k)
+    pi = np.tile(np.arange(k), len(sub))
+    ref = oracle.sample_paths(oracle.ANISO_2D, sub, ni, pi, h, seed=1234, tag=0,
+                              cv=oracle.CV_GRID, grad=oracle.build_gradient(2, v), grid_n=513)
+    prec = {}
+    for name in ("fp32", "fp64"):
+        rr = res[name]
+        phi = rr["phi"].cpu().numpy()[ni, pi].astype(np.float64)
+        xi = rr["xi"].cpu().numpy()[ni, pi].astype(np.float64)
+        st = rr["steps"].cpu().numpy()[ni, pi]
+        same = st == ref["steps"]
+        ps = float((rr["mean_steps"].cpu().numpy() * n_paths).sum())
+        prec[name] = {"exit_step_flips": int((~same).sum()), "paths_compared": int(same.size),
+                      "max_abs_err_phi": float(np.abs(phi - ref["phi"])[same].max()),
+                      "max_abs_err_xi": float(np.abs(xi - ref["xi"])[same].max()),
+                      "path_steps_per_s": ps / (tms[name] / 1e3)}
+    m32 = res["fp32"]["mean_cv"].cpu().numpy()
+    m64 = res["fp64"]["mean_cv"].cpu().numpy()
+    se = res["fp64"]["se_cv"].cpu().numpy()
+    ok = se > 0  # nodes whose paths all finish at k = 0 have SE = 0
+    prec["node_mean_fp32_vs_fp64"] = {"max_abs": float(np.abs(m32 - m64).max()),
+                                      "max_over_se": float((np.abs(m32 - m64)[ok] / se[ok]).max())}
+    u = W.exact_u(1, nodes.astype(np.float64))
+    out = {"workload": "c4", "metric": METRIC, "value": work * len(ms) / (sum(ms) / 1e3),
+           "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+           "data": "synthetic", "ms_per_step": sum(ms) / len(ms),
+           "config": {"workload": "anisotropic 2D A=[[1,.5],[.5,1]](1+sin(2 pi x)/2), 32x32 "
+                                  "subdomains, 31744 nodes x 1e4 paths, dt=1e-4, eps=1e-2 grid "
+                                  "513^2; precision study on 256 nodes"},
+           "rmse_fp32_full": float(np.sqrt(np.mean((r["mean_cv"] - u) ** 2))),
+           "precision": prec, "clocks": clk}
+    p32.close()
+    p64.close()
+    ctx.close()
+    return out
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_info()
+    if args.workload != "c1" and args.impl == "ours":
+        if rank == 0:
+            fn = {"c2": run_c2, "c3": run_c3, "c4": run_c4}[args.workload]
+            print(json.dumps(fn(args)), flush=True)
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
