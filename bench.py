@@ -448,10 +448,13 @@ def run_c2(args):
     for slot, lv in enumerate(levels_cfg):
         prob.set_control_grid(slot, W.control_grid(2, 65, lv["eps"]))
     nodes = W.workload_nodes("c2")
+    div = 1
+    if args.small:  # profiling case: 1/16 of the nodes, 1/10 of the paths
+        nodes, div = nodes[::16].copy(), 10
     cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).to(dev) for j in range(3)]
-    lv = [dict(nodes=cols, n_paths=c["n_paths"], dt=c["dt"], grid_id=i, stream_tag=1 + i)
+    lv = [dict(nodes=cols, n_paths=c["n_paths"] // div, dt=c["dt"], grid_id=i, stream_tag=1 + i)
           for i, c in enumerate(levels_cfg)]
-    lv.append(dict(nodes=cols, n_paths=levels_cfg[0]["n_paths"], dt=levels_cfg[0]["dt"],
+    lv.append(dict(nodes=cols, n_paths=levels_cfg[0]["n_paths"] // div, dt=levels_cfg[0]["dt"],
                    grid_id=pdd.PDD_CV_NONE, stream_tag=1))
     prepared = [prob._prepare(l["nodes"], l["n_paths"], l["dt"], l["grid_id"], SEED,
                               l["stream_tag"], 1.0, False, True, False, False) for l in lv]

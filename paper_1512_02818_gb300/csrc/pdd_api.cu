@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/pdd.h"
+#include "pdd_device.cuh"
 #include "pdd_internal.h"
 
 namespace pdd {
@@ -755,12 +756,20 @@ int pdd_set_control_grid(pdd_problem* p, int grid_id, const pdd_grid_desc* d) {
                         c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   }
+  // one allocation: the nodal gradient table, then the per-cell coefficients
   void* table = nullptr;
-  const size_t tbytes = npts * (dim == 2 ? sizeof(float2) : sizeof(float4));
+  const size_t m = (size_t)d->n - 1;
+  const size_t ncell = dim == 2 ? m * m : m * m * m;
+  const size_t tbytes = cell_table_offset(d->n, dim) + ncell * (dim == 2 ? 32 : 96);
   if (e == cudaSuccess) e = cudaMalloc(&table, tbytes);
   if (e == cudaSuccess) {
     e = d->kind == PDD_GRID_VALUES ? launch_grid_gradient(staged, d->n, dim, table, c->stream)
                                    : launch_grid_pack(staged, d->n, dim, table, c->stream);
+    c->launches += 1;
+  }
+  if (e == cudaSuccess) {
+    e = launch_grid_cells(table, d->n, dim, (char*)table + cell_table_offset(d->n, dim),
+                          c->stream);
     c->launches += 1;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -301,6 +301,63 @@ __device__ __forceinline__ void grid_grad_3d(const float4* __restrict__ G, int n
 }
 
 // ---------------------------------------------------------------------------
+// Cell-coefficient tables (FP32 paths).  For every grid cell the multilinear
+// interpolant of each gradient component is stored as polynomial coefficients
+// in the cell's local coordinates (fx, fy[, fz]) in [0,1]:
+//   2D: g = c0 + c1 fx + c2 fy + c3 fx fy                  (2 x float4 = 32 B)
+//   3D: g = c000 + c100 fx + c010 fy + c001 fz + c110 fx fy + c101 fx fz
+//           + c011 fy fz + c111 fx fy fz                      (6 x float4 = 96 B)
+// so a lane reads one contiguous 32 B / 96 B record per step instead of 4 / 8
+// scattered corner values.  The values equal the multilinear interpolation of
+// the nodal table up to the FP32 rounding of the coefficients.
+// Layout of a 3D record: [x: c000 c100 c010 c001 | x: c110 c101 c011 c111 |
+// the same for y | for z].  The table follows the nodal table in the grid's
+// allocation, at offset cell_table_offset(n, dim).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ size_t cell_table_offset(int n, int dim) {
+  const size_t pts = dim == 2 ? (size_t)n * n : (size_t)n * n * n;
+  const size_t bytes = pts * (dim == 2 ? 8 : 16);
+  return (bytes + 255) / 256 * 256;
+}
+
+template <class T>
+__device__ __forceinline__ void grid_cells_2d(const float4* __restrict__ C, int n, T x, T y,
+                                              T& gx, T& gy) {
+  const T s = (T)(n - 1);
+  T fx, fy;
+  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy);
+  const float4* p = C + 2 * ((size_t)iy * (n - 1) + ix);
+  const float4 a = __ldg(p), b = __ldg(p + 1);
+  gx = (a.x + fx * a.y) + fy * (a.z + fx * a.w);
+  gy = (b.x + fx * b.y) + fy * (b.z + fx * b.w);
+}
+
+template <class T>
+__device__ __forceinline__ T cell_poly3(const float4 lo, const float4 hi, T fx, T fy, T fz) {
+  // lo = (c000, c100, c010, c001), hi = (c110, c101, c011, c111)
+  const T a = lo.x + fz * lo.w;  // c000 + c001 fz
+  const T b = lo.z + fz * hi.z;  // c010 + c011 fz
+  const T c = lo.y + fz * hi.y;  // c100 + c101 fz
+  const T d = hi.x + fz * hi.w;  // c110 + c111 fz
+  return (a + fy * b) + fx * (c + fy * d);
+}
+
+template <class T>
+__device__ __forceinline__ void grid_cells_3d(const float4* __restrict__ C, int n, T x, T y, T z,
+                                              T& gx, T& gy, T& gz) {
+  const T s = (T)(n - 1);
+  T fx, fy, fz;
+  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy), iz = cell_of(z * s, n, fz);
+  const size_t m = (size_t)(n - 1);
+  const float4* p = C + 6 * (((size_t)iz * m + iy) * m + ix);
+  const float4 x0 = __ldg(p), x1 = __ldg(p + 1), y0 = __ldg(p + 2), y1 = __ldg(p + 3);
+  const float4 z0 = __ldg(p + 4), z1 = __ldg(p + 5);
+  gx = cell_poly3<T>(x0, x1, fx, fy, fz);
+  gy = cell_poly3<T>(y0, y1, fx, fy, fz);
+  gz = cell_poly3<T>(z0, z1, fx, fy, fz);
+}
+
+// ---------------------------------------------------------------------------
 // Compensated (Kahan) summation for the FP32 Z and xi accumulators.
 // ---------------------------------------------------------------------------
 template <class T>

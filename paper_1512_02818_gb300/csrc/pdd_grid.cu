@@ -55,6 +55,54 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ src, double* __restr
   if (i < count) dst[i] = (double)src[i];
 }
 
+// Multilinear polynomial coefficients of every cell, from the FP32 nodal table
+// (promoted to FP64), rounded to FP32.  Record layouts: see pdd_device.cuh.
+__global__ void grid_cells_kernel(const void* __restrict__ nodal, int n, int dim,
+                                  float4* __restrict__ cells) {
+  const long long m = n - 1;
+  const long long ncell = dim == 2 ? m * m : m * m * m;
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const long long nn = n;
+  if (dim == 2) {
+    const long long ix = c % m, iy = c / m;
+    const float2* G = (const float2*)nodal;
+    const float2 g00 = G[iy * nn + ix], g10 = G[iy * nn + ix + 1];
+    const float2 g01 = G[(iy + 1) * nn + ix], g11 = G[(iy + 1) * nn + ix + 1];
+    const double a[2][4] = {{g00.x, g10.x, g01.x, g11.x}, {g00.y, g10.y, g01.y, g11.y}};
+    for (int comp = 0; comp < 2; ++comp) {
+      const double v00 = a[comp][0], v10 = a[comp][1], v01 = a[comp][2], v11 = a[comp][3];
+      cells[2 * c + comp] = make_float4((float)v00, (float)(v10 - v00), (float)(v01 - v00),
+                                        (float)(v11 - v10 - v01 + v00));
+    }
+    return;
+  }
+  const long long ix = c % m, iy = (c / m) % m, iz = c / (m * m);
+  const float4* G = (const float4*)nodal;
+  float4 g[2][2][2];  // [dz][dy][dx]
+  for (int dz = 0; dz < 2; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx)
+        g[dz][dy][dx] = G[((iz + dz) * nn + (iy + dy)) * nn + ix + dx];
+  for (int comp = 0; comp < 3; ++comp) {
+    auto v = [&](int dx, int dy, int dz) -> double {
+      const float4 q = g[dz][dy][dx];
+      return comp == 0 ? q.x : (comp == 1 ? q.y : q.z);
+    };
+    const double c000 = v(0, 0, 0);
+    const double c100 = v(1, 0, 0) - c000;
+    const double c010 = v(0, 1, 0) - c000;
+    const double c001 = v(0, 0, 1) - c000;
+    const double c110 = v(1, 1, 0) - v(1, 0, 0) - v(0, 1, 0) + c000;
+    const double c101 = v(1, 0, 1) - v(1, 0, 0) - v(0, 0, 1) + c000;
+    const double c011 = v(0, 1, 1) - v(0, 1, 0) - v(0, 0, 1) + c000;
+    const double c111 = v(1, 1, 1) - v(1, 1, 0) - v(1, 0, 1) - v(0, 1, 1) + v(1, 0, 0) +
+                        v(0, 1, 0) + v(0, 0, 1) - c000;
+    cells[6 * c + 2 * comp] = make_float4((float)c000, (float)c100, (float)c010, (float)c001);
+    cells[6 * c + 2 * comp + 1] = make_float4((float)c110, (float)c101, (float)c011, (float)c111);
+  }
+}
+
 static unsigned blocks_for(long long count, unsigned threads) {
   return (unsigned)((count + threads - 1) / threads);
 }
@@ -77,4 +125,13 @@ cudaError_t launch_f32_to_f64(const float* src, double* dst, size_t count, cudaS
   return cudaGetLastError();
 }
 
+}  // namespace pdd
+
+namespace pdd {
+cudaError_t launch_grid_cells(const void* nodal, int n, int dim, void* cells, cudaStream_t st) {
+  const long long m = n - 1;
+  const long long ncell = dim == 2 ? m * m : m * m * m;
+  grid_cells_kernel<<<blocks_for(ncell, 256), 256, 0, st>>>(nodal, n, dim, (float4*)cells);
+  return cudaGetLastError();
+}
 }  // namespace pdd

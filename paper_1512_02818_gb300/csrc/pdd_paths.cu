@@ -26,8 +26,12 @@ namespace pdd {
 
 constexpr int kBlockThreads = 256;     // default block size
 constexpr int kMaxBlockThreads = 512;  // largest block size a launch may ask for
-#ifndef PDD_MIN_BLOCKS
-#define PDD_MIN_BLOCKS 1
+// Minimum resident blocks per SM requested from the compiler (register cap).
+#ifndef PDD_MIN_BLOCKS_2D
+#define PDD_MIN_BLOCKS_2D 1
+#endif
+#ifndef PDD_MIN_BLOCKS_3D
+#define PDD_MIN_BLOCKS_3D 1
 #endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 enum { kCvNone = 0, kCvGrid = 1, kCvExact = 2 };
@@ -43,19 +47,35 @@ struct PathState {
 
 // Per-lane copy of the parameters of the segment the lane's path belongs to.
 // With a single segment they are the same for every lane and never change.
-template <class T>
-struct LaneSeg {
-  T h, sqh, thr0;
-  const void* grad;
-  int gn, max_steps;
+// FP32 paths read the cell-coefficient table, FP64 paths the nodal table
+// (whose multilinear interpolation they evaluate in FP64, as the oracle does).
+#ifndef PDD_CELLS_2D
+#define PDD_CELLS_2D 1
+#endif
+#ifndef PDD_CELLS_3D
+#define PDD_CELLS_3D 1
+#endif
+template <class T, int D>
+struct UseCells {
+  static constexpr bool value =
+      sizeof(T) == 4 && ((D == 2 && PDD_CELLS_2D) || (D == 3 && PDD_CELLS_3D));
 };
 
 template <class T>
+struct LaneSeg {
+  T h, sqh, thr0;
+  const void* grad;  // the table this lane reads (cells or nodal); null: no grid
+  int gn, max_steps;
+};
+
+template <class T, int D>
 __device__ __forceinline__ void load_seg(const SegArgs& sg, LaneSeg<T>& ls) {
   ls.h = (T)sg.h;
   ls.sqh = (T)sg.sqrt_h;
   ls.thr0 = (T)sg.thr0;
   ls.grad = sg.grad;
+  if (UseCells<T, D>::value && sg.grad != nullptr)
+    ls.grad = (const char*)sg.grad + cell_table_offset(sg.grid_n, D);
   ls.gn = sg.grid_n;
   ls.max_steps = sg.max_steps;
 }
@@ -86,7 +106,7 @@ __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long
   s.Y = T(1);
   s.Z = s.Zc = s.XI = s.XIc = T(0);
   s.k = 0;
-  if (MULTI) load_seg(sg, ls);
+  if (MULTI) load_seg<T, D>(sg, ls);
 }
 
 // Finish test of Algorithm 1: d(X_k) >= -c0 |sigma^T N| sqrt(h).
@@ -128,11 +148,19 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
   if (CV != kCvNone && (CV != kCvGrid || !MULTI || ls.grad != nullptr)) {
     T gv[3] = {T(0), T(0), T(0)};
     if (CV == kCvGrid) {
-      if (D == 2)
-        grid_grad_2d<T>((const float2*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1]);
-      else
-        grid_grad_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
-                        gv[2]);
+      if (D == 2) {
+        if (UseCells<T, 2>::value)
+          grid_cells_2d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1]);
+        else
+          grid_grad_2d<T>((const float2*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1]);
+      } else {
+        if (UseCells<T, 3>::value)
+          grid_cells_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
+                           gv[2]);
+        else
+          grid_grad_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
+                          gv[2]);
+      }
     } else {
       gv[0] = o.g0;
       gv[1] = o.g1;
@@ -220,21 +248,21 @@ __device__ __forceinline__ bool refill(const PathArgs& a, PathState<T>& s, LaneS
   return __ballot_sync(kFull, active) != 0u;
 }
 
-template <class T>
+template <class T, int D>
 __device__ __forceinline__ void init_lane(const PathArgs& a, PathState<T>& s, LaneSeg<T>& ls) {
   s.x[0] = s.x[1] = s.x[2] = T(0);
   s.Y = s.Z = s.Zc = s.XI = s.XIc = T(0);
   s.k = 0;
   s.node = s.path = s.seg = 0;
-  load_seg(a.seg[0], ls);
+  load_seg<T, D>(a.seg[0], ls);
 }
 
 template <class P, class T, int CV, bool MULTI>
-__global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS)
+__global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_2D)
     paths_2d(const __grid_constant__ PathArgs a) {
   PathState<T> s;
   LaneSeg<T> ls;
-  init_lane(a, s, ls);
+  init_lane<T, 2>(a, s, ls);
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
   while (refill<T, 2, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
@@ -269,11 +297,11 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS)
 //   step 0: a0 a1 a2   step 1: a3 b0 b1   step 2: b2 b3 c0   step 3: c1 c2 c3
 // Blocks are drawn only when the path is still running.
 template <class P, class T, int CV, bool MULTI>
-__global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS)
+__global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
     paths_3d(const __grid_constant__ PathArgs a) {
   PathState<T> s;
   LaneSeg<T> ls;
-  init_lane(a, s, ls);
+  init_lane<T, 3>(a, s, ls);
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
   while (refill<T, 3, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {

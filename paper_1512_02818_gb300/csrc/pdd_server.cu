@@ -51,7 +51,6 @@ class Arena {
   void reset(size_t size) {
     free_.clear();
     if (size) free_[0] = size;
-    size_ = size;
   }
   bool alloc(size_t bytes, size_t* off) {
     bytes = align256(bytes);
@@ -83,11 +82,9 @@ class Arena {
       }
     }
   }
-  size_t size() const { return size_; }
 
  private:
   std::map<size_t, size_t> free_;
-  size_t size_ = 0;
 };
 
 enum class RState { kPending, kActive, kFinishing, kDone, kFailed, kCancelled };
