@@ -762,6 +762,14 @@ int pdd_set_control_grid(pdd_problem* p, int grid_id, const pdd_grid_desc* d) {
   const size_t ncell = dim == 2 ? m * m : m * m * m;
   const size_t tbytes = cell_table_offset(d->n, dim) + ncell * (dim == 2 ? 32 : 96);
   if (e == cudaSuccess) e = cudaMalloc(&table, tbytes);
+  // cell records are read with 32-byte vector loads: the table must start on a
+  // 32-byte boundary (cudaMalloc gives 256; the offset is a multiple of 256)
+  if (e == cudaSuccess && (((uintptr_t)table | cell_table_offset(d->n, dim)) & 31u) != 0) {
+    cudaFree(table);
+    cudaFree(staged);
+    set_error("pdd_set_control_grid: misaligned table");
+    return PDD_ERR_CUDA;
+  }
   if (e == cudaSuccess) {
     e = d->kind == PDD_GRID_VALUES ? launch_grid_gradient(staged, d->n, dim, table, c->stream)
                                    : launch_grid_pack(staged, d->n, dim, table, c->stream);

@@ -320,6 +320,17 @@ __host__ __device__ __forceinline__ size_t cell_table_offset(int n, int dim) {
   return (bytes + 255) / 256 * 256;
 }
 
+// 32-byte load through the non-coherent (read-only) path: one 256-bit vector
+// load per record chunk, so a lane's chunk is one full sector.  `p` must be
+// 32-byte aligned (records start at multiples of 32 bytes of a 256-byte
+// aligned table).
+__device__ __forceinline__ void ldg_v8(const float4* p, float4& a, float4& b) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z),
+                 "=f"(b.w)
+               : "l"(p));
+}
+
 template <class T>
 __device__ __forceinline__ void grid_cells_2d(const float4* __restrict__ C, int n, T x, T y,
                                               T& gx, T& gy) {
@@ -327,7 +338,8 @@ __device__ __forceinline__ void grid_cells_2d(const float4* __restrict__ C, int 
   T fx, fy;
   const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy);
   const float4* p = C + 2 * ((size_t)iy * (n - 1) + ix);
-  const float4 a = __ldg(p), b = __ldg(p + 1);
+  float4 a, b;
+  ldg_v8(p, a, b);
   gx = (a.x + fx * a.y) + fy * (a.z + fx * a.w);
   gy = (b.x + fx * b.y) + fy * (b.z + fx * b.w);
 }
@@ -350,8 +362,10 @@ __device__ __forceinline__ void grid_cells_3d(const float4* __restrict__ C, int 
   const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy), iz = cell_of(z * s, n, fz);
   const size_t m = (size_t)(n - 1);
   const float4* p = C + 6 * (((size_t)iz * m + iy) * m + ix);
-  const float4 x0 = __ldg(p), x1 = __ldg(p + 1), y0 = __ldg(p + 2), y1 = __ldg(p + 3);
-  const float4 z0 = __ldg(p + 4), z1 = __ldg(p + 5);
+  float4 x0, x1, y0, y1, z0, z1;
+  ldg_v8(p, x0, x1);
+  ldg_v8(p + 2, y0, y1);
+  ldg_v8(p + 4, z0, z1);
   gx = cell_poly3<T>(x0, x1, fx, fy, fz);
   gy = cell_poly3<T>(y0, y1, fx, fy, fz);
   gz = cell_poly3<T>(z0, z1, fx, fy, fz);

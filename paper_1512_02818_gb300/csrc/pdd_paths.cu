@@ -31,7 +31,7 @@ constexpr int kMaxBlockThreads = 512;  // largest block size a launch may ask fo
 #define PDD_MIN_BLOCKS_2D 1
 #endif
 #ifndef PDD_MIN_BLOCKS_3D
-#define PDD_MIN_BLOCKS_3D 1
+#define PDD_MIN_BLOCKS_3D 2  // 64 registers: twice the warps of the unconstrained 3D kernel
 #endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 enum { kCvNone = 0, kCvGrid = 1, kCvExact = 2 };
