@@ -586,6 +586,24 @@ def run_c3(args):
     cal_s = time.perf_counter() - tc
     srv.close()
     cal_rate = float((res["mean_steps"] * res["n_paths"]).sum()) / cal_s
+    # served form at a fixed RMSE: N per request from the pilot variances
+    # (balanced choice, stat^2 <= a^2/2 at every node), plain vs eps = 1e-2 CV
+    a_t = 2e-3
+    u = W.exact_u(0, cal_nodes.astype(np.float64))
+    fixed = {}
+    for name, gid, var in (("plain", pdd.PDD_CV_NONE, res["var_phi"]),
+                           ("cv_eps1e-2", 1, res["var_cv"])):
+        n_req = int(np.ceil(np.max(var) / (a_t**2 / 2.0)))
+        srv = pdd.Server(ctx, max_active=32, max_queue=64, device_arena_bytes=1 << 30)
+        tc = time.perf_counter()
+        t = srv.submit(prob, cal_nodes, n_req, DT, grid_id=gid, seed=SEED, stream_tag=77)
+        st, rr = srv.poll(t, len(cal_nodes), int(3600e6))
+        secs = time.perf_counter() - tc
+        srv.close()
+        mean = rr["mean_phi"] if gid == pdd.PDD_CV_NONE else rr["mean_cv"]
+        fixed[name] = {"n_paths": n_req, "seconds": secs, "nodes_per_s": len(cal_nodes) / secs,
+                       "rmse_vs_exact": float(np.sqrt(np.mean((mean - u) ** 2)))}
+    fixed["cv_speedup_nodes_per_s"] = fixed["cv_eps1e-2"]["nodes_per_s"] / fixed["plain"]["nodes_per_s"]
     sat = serve(args.rate, args.window, 30.0, 11)
     # capacity in requests/s: sustained rate over the mean offered request size
     reqs = W.serving_requests(11, args.rate, args.window)
@@ -604,6 +622,7 @@ def run_c3(args):
                                    "max_queue 64, quantum 8e9 path-steps"},
             "saturation": sat, "at_0.7x_capacity": steady,
             "served_rate_one_request_path_steps_per_s": cal_rate,
+            "fixed_rmse_served": {"target_rmse": a_t, **fixed},
             "mean_request_path_steps_est": float(mean_req),
             "capacity_requests_per_s_est": cap, "clocks": clk}
 

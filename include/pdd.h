@@ -234,6 +234,26 @@ int pdd_estimate_nodes(pdd_problem* problem, const pdd_estimate_args* args, pdd_
 int pdd_estimate_levels(pdd_problem* problem, int n_levels, const pdd_estimate_args* levels,
                         pdd_node_stats* outs, uint32_t flags);
 
+/* Exact node records, for checkpoint / resume and for merging runs.  A node
+   record is PDD_RECORD_WORDS uint64 words of exact integer sums (128-bit sums
+   of the fixed-point scores, their squares and product, the exit indices and
+   their squares, the path count and the truncation count).  Records add
+   element-wise with carries (pdd_records_merge), so paths can be split over
+   calls, processes or GPUs in any way and merged into the same bits.
+   pdd_accumulate runs paths path_offset .. path_offset + args->n_paths - 1 of
+   every node (same random streams as pdd_estimate_nodes) and adds their sums
+   into `records` (device, n_nodes x PDD_RECORD_WORDS, zeroed by the caller
+   before the first call); synchronous unless args->flags has PDD_FLAG_ASYNC.
+   pdd_finalize_records turns records (device) into the statistics of
+   pdd_estimate_nodes (out: host or device per out->on_device).
+   pdd_records_merge adds n_nodes host records `src` into host records `dst`. */
+#define PDD_RECORD_WORDS 16
+int pdd_accumulate(pdd_problem* problem, const pdd_estimate_args* args, uint64_t path_offset,
+                   uint64_t* records);
+int pdd_finalize_records(pdd_ctx* ctx, const uint64_t* records, int64_t n_nodes, double kappa,
+                         pdd_node_stats* out);
+int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes);
+
 /* Autotuner: runs `sample` (device coordinates) under candidate launch shapes
    (128/256/512 threads per block, full and half occupancy), times each with
    CUDA events on the context's stream, and keeps the fastest as the context's

@@ -824,6 +824,150 @@ int pdd_estimate_levels(pdd_problem* p, int n_levels, const pdd_estimate_args* l
   return estimate_impl(p, n_levels, levels, outs, flags, "pdd_estimate_levels");
 }
 
+int pdd_accumulate(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_offset,
+                   uint64_t* records) {
+  if (!p || !a || !records) {
+    set_error("pdd_accumulate: NULL argument");
+    return PDD_ERR_INVALID;
+  }
+  LevelPlan lp;
+  pdd_node_stats dummy{};
+  int rc = check_level(p, a, &dummy, "pdd_accumulate", 0, &lp);
+  if (rc != PDD_OK) return rc;
+  if (a->flags & PDD_FLAG_EMIT_PATHS) {
+    set_error("pdd_accumulate: per-path output is not available here");
+    return PDD_ERR_INVALID;
+  }
+  if (!a->coords_on_device) {
+    set_error("pdd_accumulate: coordinates must be device pointers");
+    return PDD_ERR_INVALID;
+  }
+  if (path_offset + (uint64_t)a->n_paths > (1ull << 32)) {
+    set_error("pdd_accumulate: path indices beyond 2^32");
+    return PDD_ERR_INVALID;
+  }
+  if (a->n_nodes == 0) return PDD_OK;
+  pdd_ctx* c = p->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  rc = ensure_workspace(c, 256);
+  if (rc != PDD_OK) return rc;
+  WsHeader* hdr = (WsHeader*)c->ws;
+  PathArgs pa{};
+  pa.cursor = &hdr->cursor;
+  pa.err = &hdr->err;
+  pa.trunc_total = &hdr->trunc_total;
+  pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
+  pa.max_blocks = c->max_blocks;
+  pa.block_threads = c->block_threads;
+  pa.n_segs = 1;
+  SegArgs& sg = pa.seg[0];
+  const int dim = p->dim;
+  sg.cx = a->coords[0];
+  sg.cy = a->coords[1];
+  sg.cz = dim == 3 ? a->coords[2] : a->coords[0];
+  sg.begin = 0;
+  sg.total = (unsigned long long)a->n_nodes * (unsigned long long)a->n_paths;
+  sg.n_paths = (unsigned long long)a->n_paths;
+  sg.acc = (unsigned long long*)records;
+  sg.grad = lp.table;
+  sg.emit_stride = 0;
+  sg.h = a->dt;
+  sg.sqrt_h = std::sqrt(a->dt);
+  const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
+  sg.thr0 = c0 * sg.sqrt_h;
+  sg.path_off = (uint32_t)path_offset;
+  sg.key0 = (uint32_t)a->seed;
+  sg.key1 = a->stream_tag;
+  sg.seed_hi = (uint32_t)(a->seed >> 32);
+  sg.grid_n = lp.grid_n;
+  sg.max_steps = (int)lp.max_steps;
+  pa.total = sg.total;
+  PDD_CUDA(cudaMemsetAsync(hdr, 0, 256, c->stream), "cudaMemsetAsync");
+  int blocks = 0;
+  PDD_CUDA(launch_paths(p->desc.kind, p->desc.precision, lp.cv, pa, c->num_sms, c->stream, &blocks),
+           "path kernel launch");
+  c->launches += 1;
+  if (a->flags & PDD_FLAG_ASYNC) return PDD_OK;
+  WsHeader h{};
+  PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+           "cudaMemcpyAsync(header)");
+  PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (h.err & kErrOverflow) {
+    set_error("pdd_accumulate: a score left the fixed-point range |score| < 32768");
+    return PDD_ERR_OVERFLOW;
+  }
+  if (h.trunc_total > 0) {
+    set_error("pdd_accumulate: %llu paths hit max_steps", h.trunc_total);
+    return PDD_WARN_TRUNCATED;
+  }
+  return PDD_OK;
+}
+
+int pdd_finalize_records(pdd_ctx* c, const uint64_t* records, int64_t n_nodes, double kappa,
+                         pdd_node_stats* out) {
+  if (!c || !records || !out || n_nodes < 0 || n_nodes >= ((int64_t)1 << 32)) {
+    set_error("pdd_finalize_records: bad arguments");
+    return PDD_ERR_INVALID;
+  }
+  if (n_nodes == 0) return PDD_OK;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const size_t n = (size_t)n_nodes, n8 = align_up(n * 8, 256);
+  if (!out->on_device) {
+    int rc = ensure_workspace(c, 256 + 14 * n8);
+    if (rc != PDD_OK) return rc;
+  }
+  char* stage = (char*)c->ws + 256;
+  double* const user_d[12] = {out->mean_phi, out->var_phi, out->mean_cv, out->var_cv,
+                              out->cov_phi_xi, out->var_xi, out->rho, out->se_phi, out->se_cv,
+                              out->vr, out->pred_speedup, out->mean_steps};
+  uint64_t* const user_u[2] = {out->n_paths, out->n_truncated};
+  double* d[12];
+  unsigned long long* u[2];
+  for (int i = 0; i < 12; ++i)
+    d[i] = (!out->on_device && user_d[i]) ? (double*)(stage + i * n8) : user_d[i];
+  for (int i = 0; i < 2; ++i)
+    u[i] = (!out->on_device && user_u[i]) ? (unsigned long long*)(stage + (12 + i) * n8)
+                                          : (unsigned long long*)user_u[i];
+  const StatPtrs sp{d[0], d[1], d[2], d[3], d[4], d[5], d[6], d[7], d[8], d[9], d[10], d[11],
+                    u[0], u[1]};
+  PDD_CUDA(launch_finalize((const unsigned long long*)records, (uint32_t)n,
+                           kappa > 0.0 ? kappa : 1.0, sp, c->stream),
+           "finalize launch");
+  c->launches += 1;
+  if (!out->on_device) {
+    for (int i = 0; i < 14; ++i) {
+      void* dst = i < 12 ? (void*)user_d[i] : (void*)user_u[i - 12];
+      const void* src = i < 12 ? (const void*)d[i] : (const void*)u[i - 12];
+      if (dst)
+        PDD_CUDA(cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToHost, c->stream),
+                 "cudaMemcpyAsync(outputs)");
+    }
+  }
+  PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  return PDD_OK;
+}
+
+int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes) {
+  if ((!dst || !src) && n_nodes > 0) {
+    set_error("pdd_records_merge: NULL argument");
+    return PDD_ERR_INVALID;
+  }
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    uint64_t* a = dst + i * PDD_RECORD_WORDS;
+    const uint64_t* b = src + i * PDD_RECORD_WORDS;
+    for (int w = 0; w < 14; w += 2) {  // seven 128-bit sums
+      const uint64_t lo = a[w] + b[w];
+      a[w + 1] += b[w + 1] + (lo < a[w] ? 1u : 0u);
+      a[w] = lo;
+    }
+    a[14] += b[14];
+    a[15] += b[15];
+  }
+  return PDD_OK;
+}
+
 int pdd_ctx_set_launch(pdd_ctx* c, int block_threads, int max_blocks) {
   if (!c) {
     set_error("pdd_ctx_set_launch: NULL context");

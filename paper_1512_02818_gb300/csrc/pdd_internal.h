@@ -13,6 +13,7 @@ namespace pdd {
 
 constexpr unsigned kErrOverflow = 1u;       // a score left the fixed-point range
 constexpr int kAccWords = 16;               // 64-bit words per node record
+static_assert(kAccWords == PDD_RECORD_WORDS, "node record size");
 constexpr unsigned long long kWarpBatch = 32;  // path indices a warp takes per cursor grab
 
 constexpr int kMaxSegments = 32;           // segments (levels / requests) per launch

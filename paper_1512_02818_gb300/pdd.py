@@ -31,6 +31,7 @@ PDD_CV_NONE, PDD_CV_EXACT = -1, -2
 PDD_MAX_GRIDS = 8
 PDD_FLAG_EMIT_PATHS, PDD_FLAG_ASYNC, PDD_FLAG_GRAPH = 1, 2, 4
 PDD_MAX_LEVELS = 32
+PDD_RECORD_WORDS = 16
 
 STAT_FIELDS = ["mean_phi", "var_phi", "mean_cv", "var_cv", "cov_phi_xi", "var_xi", "rho",
                "se_phi", "se_cv", "vr", "pred_speedup", "mean_steps"]
@@ -113,6 +114,11 @@ _SIGS = [
                                             ctypes.POINTER(GridDesc)]),
     ("pdd_estimate_nodes", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
                                           ctypes.POINTER(NodeStats)]),
+    ("pdd_accumulate", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
+                                      ctypes.c_uint64, ctypes.c_void_p]),
+    ("pdd_finalize_records", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_double, ctypes.POINTER(NodeStats)]),
+    ("pdd_records_merge", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     ("pdd_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerDesc),
                                          ctypes.POINTER(ctypes.c_void_p)]),
     ("pdd_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
@@ -245,6 +251,19 @@ def pdd_estimate_nodes(problem: int, args: EstimateArgs, out: NodeStats) -> int:
 PDD_NOALLOC_MAX_NODES = 4096
 
 
+def pdd_accumulate(problem: int, args: EstimateArgs, path_offset: int, records_ptr: int) -> int:
+    return _check(lib().pdd_accumulate(problem, ctypes.byref(args), path_offset, records_ptr))
+
+
+def pdd_finalize_records(ctx: int, records_ptr: int, n_nodes: int, kappa: float,
+                         out: NodeStats) -> None:
+    _check(lib().pdd_finalize_records(ctx, records_ptr, n_nodes, kappa, ctypes.byref(out)))
+
+
+def pdd_records_merge(dst_ptr: int, src_ptr: int, n_nodes: int) -> None:
+    _check(lib().pdd_records_merge(dst_ptr, src_ptr, n_nodes))
+
+
 def pdd_server_create(ctx: int, desc: ServerDesc | None = None) -> int:
     h = ctypes.c_void_p()
     _check(lib().pdd_server_create(ctx, ctypes.byref(desc) if desc is not None else None,
@@ -340,6 +359,22 @@ class Context:
 
     def graph_count(self) -> int:
         return pdd_ctx_graph_count(self.handle)
+
+    def finalize_records(self, records, kappa: float = 1.0) -> dict:
+        """Per-node statistics (CUDA tensors) of device records."""
+        torch = _torch()
+        n = records.shape[0]
+        res, out = {}, NodeStats()
+        out.on_device = 1
+        for f in STAT_FIELDS:
+            res[f] = torch.empty(n, dtype=torch.float64, device=records.device)
+            setattr(out, f, res[f].data_ptr())
+        for f in COUNT_FIELDS:
+            res[f] = torch.empty(n, dtype=torch.int64, device=records.device)
+            setattr(out, f, res[f].data_ptr())
+        torch.cuda.synchronize()
+        pdd_finalize_records(self.handle, records.data_ptr(), n, kappa, out)
+        return res
 
     def set_launch(self, block_threads: int = 0, max_blocks: int = 0) -> None:
         pdd_ctx_set_launch(self.handle, block_threads, max_blocks)
@@ -468,6 +503,14 @@ class Problem:
         st = pdd_estimate_levels(self.handle, [p[0] for p in prepared], [p[1] for p in prepared],
                                  flags)
         return st, [p[2] for p in prepared]
+
+    def accumulate(self, nodes, n_paths: int, dt: float, records, path_offset: int = 0,
+                   grid_id: int = PDD_CV_NONE, seed: int = 1234, stream_tag: int = 0):
+        """Add paths path_offset .. path_offset+n_paths-1 of every node into
+        `records` (int64 CUDA tensor of shape (n_nodes, PDD_RECORD_WORDS))."""
+        args, _, keep = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, 1.0, False,
+                                      True, False, False)
+        return pdd_accumulate(self.handle, args, path_offset, records.data_ptr())
 
     def autotune(self, nodes, n_paths: int, dt: float, grid_id: int = PDD_CV_NONE,
                  seed: int = 1234, stream_tag: int = 0):
