@@ -591,16 +591,18 @@ def run_c3(args):
     a_t = 2e-3
     u = W.exact_u(0, cal_nodes.astype(np.float64))
     fixed = {}
-    for name, gid, var in (("plain", pdd.PDD_CV_NONE, res["var_phi"]),
-                           ("cv_eps1e-2", 1, res["var_cv"])):
+    for name, grid, var in (("plain", pdd.PDD_CV_NONE, res["var_phi"]),
+                            ("cv_eps1e-2", 1, res["var_cv"])):
         n_req = int(np.ceil(np.max(var) / (a_t**2 / 2.0)))
         srv = pdd.Server(ctx, max_active=32, max_queue=64, device_arena_bytes=1 << 30)
         tc = time.perf_counter()
-        t = srv.submit(prob, cal_nodes, n_req, DT, grid_id=gid, seed=SEED, stream_tag=77)
-        st, rr = srv.poll(t, len(cal_nodes), int(3600e6))
+        t = srv.submit(prob, cal_nodes, n_req, DT, grid_id=grid, seed=SEED, stream_tag=77)
+        st, rr = srv.poll(t, len(cal_nodes), 2**31 - 1)
+        if st != pdd.PDD_OK:
+            raise RuntimeError(f"served fixed-RMSE request failed: status {st}")
         secs = time.perf_counter() - tc
         srv.close()
-        mean = rr["mean_phi"] if gid == pdd.PDD_CV_NONE else rr["mean_cv"]
+        mean = rr["mean_phi"] if grid == pdd.PDD_CV_NONE else rr["mean_cv"]
         fixed[name] = {"n_paths": n_req, "seconds": secs, "nodes_per_s": len(cal_nodes) / secs,
                        "rmse_vs_exact": float(np.sqrt(np.mean((mean - u) ** 2)))}
     fixed["cv_speedup_nodes_per_s"] = fixed["cv_eps1e-2"]["nodes_per_s"] / fixed["plain"]["nodes_per_s"]

@@ -581,7 +581,7 @@ class Server:
         out.on_device = 0
         for f in STAT_FIELDS + COUNT_FIELDS:
             setattr(out, f, res[f].ctypes.data if n_nodes else None)
-        st = pdd_poll(self.handle, ticket, out, timeout_us)
+        st = pdd_poll(self.handle, ticket, out, min(int(timeout_us), 2**31 - 1))
         return st, (res if st == PDD_OK else None)
 
     def cancel(self, ticket: int) -> None:
