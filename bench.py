@@ -50,7 +50,7 @@ ALGO_INSTR = {"plain": 110.0, "cv": 150.0}
 # DRAM bytes (read + write) per launch of the dominant kernel from the ncu
 # capture summarised in profiles/paths_2d_cv_profiling_case.md; None whenever
 # the kernel has changed since that capture.
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES = 586496
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-nodes", type=int, default=64)
     ap.add_argument("--cpu-paths", type=int, default=1000)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shape")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 64 of the 256 nodes x 2e4 paths (same kernels)")
     ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c1",
@@ -264,6 +266,10 @@ def run_ours(args, rank, world, local):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.set_stream(ctx.stream)  # events, flushes and kernels on one stream
+    # launch shape from the library's autotuner, on one full control-variate pass
+    tuned = (0, 0, None)
+    if not args.no_autotune:
+        tuned = prob.autotune(cols_dev, n_paths, DT, grid_id=1)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -375,6 +381,9 @@ def run_ours(args, rank, world, local):
         "pass_rate_path_steps_per_s": rate,
         "clocks": clk,
         "timed_kernel_launches": n_timed,
+        "launch_shape": {"block_threads": tuned[0] or 128, "max_blocks": tuned[1],
+                         "chosen_by": "pdd_autotune on the eps=1e-2 pass" if tuned[2]
+                         else "library default"},
     }
     prob.close()
     ctx.close()

@@ -197,7 +197,7 @@ int pdd_ctx_launch_count(pdd_ctx* ctx, int64_t* launches);
 /* Number of CUDA graphs captured by PDD_FLAG_GRAPH calls on this context. */
 int pdd_ctx_graph_count(pdd_ctx* ctx, int64_t* captures);
 /* Launch shape of the path kernels: block_threads (multiple of 32 in
-   [32, 512]; 0 = 256) and a cap on the grid size (0 = occupancy x SM count).
+   [32, 512]; 0 = 128) and a cap on the grid size (0 = occupancy x SM count).
    The shape changes only the speed: the results are exact sums keyed by
    (node, path), identical for every shape.                                  */
 int pdd_ctx_set_launch(pdd_ctx* ctx, int block_threads, int max_blocks);

@@ -24,7 +24,7 @@
 
 namespace pdd {
 
-constexpr int kBlockThreads = 256;     // default block size
+constexpr int kBlockThreads = 128;     // default block size (smaller blocks retire sooner as a launch drains)
 constexpr int kMaxBlockThreads = 512;  // largest block size a launch may ask for
 // Minimum resident blocks per SM requested from the compiler (register cap).
 #ifndef PDD_MIN_BLOCKS_2D
