@@ -69,8 +69,9 @@ def parse_args():
                     help="keep the library's default launch shape")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 64 of the 256 nodes x 2e4 paths (same kernels)")
-    ap.add_argument("--workload", choices=["c1", "c2", "c3", "c4"], default="c1",
-                    help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c2: 3D "
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit"], default="c1",
+                    help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c0: 24 nodes, "
+                         "plain, dt 1e-3; fit: Algorithm 3 on the 24 nodes; c2: 3D "
                          "three-level cascade in one launch (CUDA graph); c3: serving with "
                          "Poisson arrivals; c4: anisotropic 2D, FP32 vs FP64 paths")
     ap.add_argument("--window", type=float, default=10.0, help="c3: arrival window (s)")
@@ -720,12 +721,81 @@ def run_c4(args):
     return out
 
 
+def run_c0(args):
+    """The small 2D case: 24 nodes x 1e4 paths, dt = 1e-3, plain estimator."""
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    ctx = pdd.Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    nodes = W.workload_nodes("c0")
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).cuda() for j in range(2)]
+    holder = {}
+
+    def step():
+        holder["r"] = prob.estimate(cols, 10_000, 1e-3, async_=True)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step()
+    ms = _timed_steps(torch, ctx.stream, args.steps, step, flush)
+    r = {k: v.cpu().numpy() for k, v in holder["r"].items() if torch.is_tensor(v)}
+    work = float((r["mean_steps"] * r["n_paths"]).sum())
+    u = W.exact_u(0, nodes.astype(np.float64))
+    out = {"workload": "c0", "metric": METRIC, "value": work * len(ms) / (sum(ms) / 1e3),
+           "unit": UNIT, "ms_per_step": sum(ms) / len(ms), "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "2D CFG0, 2x2 subdomains, 24 nodes x 1e4 paths, dt=1e-3, plain"},
+           "nodes_per_s": len(nodes) * len(ms) / (sum(ms) / 1e3),
+           "rmse": float(np.sqrt(np.mean((r["mean_phi"] - u) ** 2))),
+           "max_err_over_se": float(np.max(np.abs(r["mean_phi"] - u) / r["se_phi"]))}
+    prob.close()
+    ctx.close()
+    return out
+
+
+def run_fit(args):
+    """Algorithm 3 on the 24 nodes: cloud of 100 time steps in [1e-3, 1e-2],
+    1,000 paths each, psi drawn alongside from w = sin(3 pi x) sin(2 pi y)."""
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    ctx = pdd.Context(0)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    prob.set_control_grid(0, W.control_grid(0, GRID_N, 1.0) - W.control_grid(0, GRID_N, 0.0))
+    nodes = W.workload_nodes("c0")
+    prob.fit_constants(nodes, 1000, 1e-3, 1e-2, 100, grid_id=0)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = prob.fit_constants(nodes, 1000, 1e-3, 1e-2, 100, grid_id=0)
+    secs = time.perf_counter() - t0
+    cloud = r["cloud"]
+    work = float((cloud[:, :, 3] / cloud[:, :, 0]).sum() * 1000)  # E[tau_h]/h x paths
+    u = W.exact_u(0, nodes.astype(np.float64))
+    out = {"workload": "fit", "metric": METRIC, "value": work / secs, "unit": UNIT,
+           "seconds": secs, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "Algorithm 3, 24 nodes, 100 time steps in [1e-3, 1e-2], "
+                                  "1000 paths each, psi from a synthetic w grid"},
+           "E_phi_rmse_vs_exact": float(np.sqrt(np.mean((r["E_phi"] - u) ** 2))),
+           "median_beta": float(np.median(r["beta"])), "median_V_phi": float(np.median(r["V_phi"])),
+           "median_E_tau": float(np.median(r["E_tau"])), "median_K": float(np.median(r["K"])),
+           "median_rho_phi_psi": float(np.median(r["rho_phi_psi"]))}
+    prob.close()
+    ctx.close()
+    return out
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_info()
     if args.workload != "c1" and args.impl == "ours":
         if rank == 0:
-            fn = {"c2": run_c2, "c3": run_c3, "c4": run_c4}[args.workload]
+            fn = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "c4": run_c4,
+                  "fit": run_fit}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":

@@ -107,7 +107,7 @@ typedef enum { PDD_DTYPE_F32 = 0, PDD_DTYPE_F64 = 1 } pdd_dtype;
 #define PDD_FLAG_ASYNC 2u      /* device inputs/outputs only: return once enqueued */
 #define PDD_FLAG_GRAPH 4u      /* pdd_estimate_levels: capture the launch sequence in a CUDA
                                   graph and replay it while the arguments repeat */
-#define PDD_MAX_LEVELS 32      /* levels (or batches) per pdd_estimate_levels call */
+#define PDD_MAX_LEVELS 128     /* levels (or batches) per pdd_estimate_levels call */
 
 typedef struct pdd_ctx pdd_ctx;
 typedef struct pdd_problem pdd_problem;
@@ -254,6 +254,43 @@ int pdd_finalize_records(pdd_ctx* ctx, const uint64_t* records, int64_t n_nodes,
                          pdd_node_stats* out);
 int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes);
 
+/* Fast fit of nodal constants (Algorithm 3, Sec. 5 H5).  For every node the
+   library runs n_paths realisations of Algorithm 1 at each of n_h equispaced
+   time steps h_max = h_1 > ... > h_{n_h} = h_min (the "cloud"), drawing the
+   auxiliary variate psi = -int Y sigma^T grad(w) . dW alongside, where grad(w)
+   is control grid `grid_id` (PDD_CV_NONE: no auxiliary variate), all (node, h)
+   pairs in persistent launches of up to PDD_MAX_LEVELS time steps each
+   (stream_tag_base + j keys time step j).  Per node it then fits
+     first moments  E[eta_h] = E[eta_0] + B h^delta    (normal noise, identity
+                    link: ordinary least squares) for eta = phi, tau, phi psi;
+     variances      E[V[eta_h]] = V[eta_0] + B h^delta (gamma noise, identity
+                    link: iteratively reweighted least squares) for phi, psi;
+   and returns E[phi], beta, V[phi], alpha, E[tau], K = 4 q^2 E[tau]
+   (2|beta|)^(1/delta) (eq. F:Pointwise_cost), Cov[phi,psi], V[psi] and
+   rho[phi,psi].  Output arrays are host arrays of n_nodes (any may be NULL);
+   `cloud` (nullable, host, n_nodes x n_h x 6) receives h, E[phi_h],
+   V[phi_h], E[tau_h], Cov[phi_h,psi_h], V[psi_h].                          */
+typedef struct {
+  int64_t n_nodes;
+  const float* coords[3];   /* device SoA coordinates */
+  int32_t grid_id;          /* grid of grad(w) for psi, or PDD_CV_NONE */
+  int32_t n_h;              /* time steps in the cloud, 2 .. 4096 */
+  double h_min, h_max;      /* 0 < h_min < h_max */
+  int64_t n_paths;          /* realisations per (node, h) */
+  double delta;             /* weak order: 1 (Gobet-Menozzi), 0.5 (naive test) */
+  double q;                 /* confidence factor of the balanced simulation (eq. F:N_y_h) */
+  uint64_t seed;
+  uint32_t stream_tag_base;
+  uint32_t reserved;
+} pdd_fit_args;
+
+typedef struct {
+  double *E_phi, *beta, *V_phi, *alpha, *E_tau, *K, *cov_phi_psi, *V_psi, *rho_phi_psi;
+  double* cloud;
+} pdd_fit_out;
+
+int pdd_fit_constants(pdd_problem* problem, const pdd_fit_args* args, pdd_fit_out* out);
+
 /* Autotuner: runs `sample` (device coordinates) under candidate launch shapes
    (128/256/512 threads per block, full and half occupancy), times each with
    CUDA events on the context's stream, and keeps the fastest as the context's
@@ -274,7 +311,7 @@ int pdd_autotune(pdd_problem* problem, const pdd_estimate_args* sample, int* bes
    thread owned by the server issues launches on two streams of its own and
    polls CUDA events; nothing on the device waits.                          */
 typedef struct {
-  int32_t max_active;          /* requests in the running batch, 1..32 (0: 32) */
+  int32_t max_active;          /* requests in the running batch, 1..128 (0: 32) */
   int32_t max_queue;           /* pending requests before PDD_ERR_BUSY (0: 256) */
   int64_t quantum_path_steps;  /* target path-steps per launch (0: 8e9) */
   size_t device_arena_bytes;   /* device memory for admitted requests (0: 256 MiB);

@@ -259,3 +259,83 @@ def node_stats(phi, xi, steps, kappa: float = 1.0) -> dict:
     lib.or_node_stats(n, _ptr(phi), _ptr(xi), _ptr(steps), _ptr(tr), _ptr(iso), float(kappa),
                       _ptr(st))
     return {name: st[j] for j, name in enumerate(STAT_NAMES)}
+
+
+# ---------------------------------------------------------------------------
+# Fast fit of nodal constants (Sec. 5 H5, Algorithm 3), plain numpy.
+# ---------------------------------------------------------------------------
+def ols_fit(x, y):
+    """(intercept, slope) of y = a + b x: the normal-noise, identity-link GLM
+    of the first-moment model, i.e. ordinary least squares."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    xm, ym = x.mean(), y.mean()
+    sxx = float(((x - xm) ** 2).sum())
+    b = float(((x - xm) * (y - ym)).sum()) / sxx if sxx > 0 else 0.0
+    return ym - b * xm, b
+
+
+def gamma_identity_fit(x, y, iters=200):
+    """(intercept, slope) of E[y] = a + b x for gamma-distributed y (variance
+    proportional to the mean squared), identity link: Fisher scoring, i.e.
+    weighted least squares with weights 1/mu^2 recomputed from each fit."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    a, b = ols_fit(x, y)
+    floor_mu = max(np.abs(y).min() * 1e-6, 1e-300)
+    for _ in range(iters):
+        mu = np.maximum(a + b * x, floor_mu)
+        w = 1.0 / mu**2
+        X = np.stack([np.ones_like(x), x], 1)
+        A = X.T @ (w[:, None] * X)
+        rhs = X.T @ (w * y)
+        na, nb = np.linalg.solve(A, rhs)
+        done = abs(na - a) + abs(nb - b) <= 1e-14 * (abs(na) + abs(nb) + 1e-300)
+        a, b = float(na), float(nb)
+        if done:
+            break
+    return a, b
+
+
+def h_cloud(h_min, h_max, n_h):
+    """Equispaced time steps h_max = h_1 > ... > h_{n_h} = h_min."""
+    return np.array([h_max - (h_max - h_min) * j / (n_h - 1) for j in range(n_h)])
+
+
+def fit_constants(kind, nodes, n_paths, h_min, h_max, n_h, delta=1.0, q=2.0, seed=1234,
+                  tag_base=0, cv=CV_NONE, grad=None, grid_n=0, c0=GOBET_MENOZZI_C0):
+    """Algorithm 3: per node, n_paths realisations at every h of the cloud
+    (random streams keyed by tag_base + j for step j), then the moment fits.
+    Returns a dict of per-node arrays and the cloud (n_nodes, n_h, 6):
+    h, E[phi_h], V[phi_h], E[tau_h], Cov[phi_h, psi_h], V[psi_h]."""
+    hs = h_cloud(h_min, h_max, n_h)
+    dim = problem_dim(kind)
+    nodes = np.asarray(nodes, dtype=np.float64).reshape(-1, dim)
+    n = nodes.shape[0]
+    cloud = np.zeros((n, n_h, 6))
+    for j, h in enumerate(hs):
+        r = estimate_nodes(kind, nodes, n_paths, h, seed=seed, tag=tag_base + j, cv=cv,
+                           grad=grad, grid_n=grid_n, c0=c0, per_path=False)
+        cloud[:, j, 0] = h
+        cloud[:, j, 1] = r["mean_phi"]
+        cloud[:, j, 2] = r["var_phi"]
+        cloud[:, j, 3] = r["mean_steps"] * h
+        cloud[:, j, 4] = r["cov_phi_xi"]
+        cloud[:, j, 5] = r["var_xi"]
+    x = hs**delta
+    out = {k: np.zeros(n) for k in ("E_phi", "beta", "V_phi", "alpha", "E_tau", "K",
+                                     "cov_phi_psi", "V_psi", "rho_phi_psi")}
+    for i in range(n):
+        out["E_phi"][i], out["beta"][i] = ols_fit(x, cloud[i, :, 1])
+        out["E_tau"][i], _ = ols_fit(x, cloud[i, :, 3])
+        out["V_phi"][i], out["alpha"][i] = gamma_identity_fit(x, cloud[i, :, 2])
+        if cv != CV_NONE:
+            out["cov_phi_psi"][i], _ = ols_fit(x, cloud[i, :, 4])
+            out["V_psi"][i], _ = gamma_identity_fit(x, cloud[i, :, 5])
+        else:
+            out["cov_phi_psi"][i] = out["V_psi"][i] = np.nan
+        out["rho_phi_psi"][i] = out["cov_phi_psi"][i] / np.sqrt(out["V_phi"][i] * out["V_psi"][i])
+        # nodal cost constant of eq. F:Pointwise_cost
+        out["K"][i] = 4 * q * q * out["E_tau"][i] * (2 * abs(out["beta"][i])) ** (1 / delta)
+    out["cloud"] = cloud
+    return out

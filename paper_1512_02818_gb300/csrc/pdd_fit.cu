@@ -1,0 +1,192 @@
+// pdd_fit.cu -- fast fit of nodal constants (Bernal & Acebron, Sec. 5 H5 and
+// Algorithm 3): all (node, h) pairs of an h-cloud run as levels of the
+// persistent path kernel; the per-node fits are small host-side regressions.
+//   first moments: E[eta_h] = E[eta_0] + B h^delta, normal noise and identity
+//     link, i.e. ordinary least squares in x = h^delta;
+//   variances: E[V[eta_h]] = V[eta_0] + B h^delta, gamma noise and identity
+//     link, i.e. iteratively reweighted least squares with weights 1/mu^2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "../../include/pdd.h"
+#include "pdd_internal.h"
+
+namespace pdd {
+void set_error(const char* fmt, ...);
+}
+
+using namespace pdd;
+
+namespace {
+
+// y = a + b x by ordinary least squares.
+void ols(const std::vector<double>& x, const std::vector<double>& y, double* a, double* b) {
+  const size_t m = x.size();
+  double mx = 0, my = 0;
+  for (size_t j = 0; j < m; ++j) {
+    mx += x[j];
+    my += y[j];
+  }
+  mx /= (double)m;
+  my /= (double)m;
+  double sxy = 0, sxx = 0;
+  for (size_t j = 0; j < m; ++j) {
+    sxy += (x[j] - mx) * (y[j] - my);
+    sxx += (x[j] - mx) * (x[j] - mx);
+  }
+  *b = sxx > 0 ? sxy / sxx : 0.0;
+  *a = my - *b * mx;
+}
+
+// mu = a + b x for gamma-distributed y (variance proportional to mu^2), identity
+// link: weighted least squares with weights 1/mu^2 from the previous fit until
+// the coefficients settle (Fisher scoring for this model).
+void gamma_identity(const std::vector<double>& x, const std::vector<double>& y, double* a,
+                    double* b) {
+  ols(x, y, a, b);
+  const size_t m = x.size();
+  double ymin = 1e300;
+  for (double v : y) ymin = std::min(ymin, std::fabs(v));
+  const double floor_mu = std::max(ymin * 1e-6, 1e-300);
+  for (int it = 0; it < 200; ++it) {
+    double sw = 0, swx = 0, swy = 0, swxx = 0, swxy = 0;
+    for (size_t j = 0; j < m; ++j) {
+      const double mu = std::max(*a + *b * x[j], floor_mu);
+      const double w = 1.0 / (mu * mu);
+      sw += w;
+      swx += w * x[j];
+      swy += w * y[j];
+      swxx += w * x[j] * x[j];
+      swxy += w * x[j] * y[j];
+    }
+    const double det = sw * swxx - swx * swx;
+    if (!(det > 0)) break;
+    const double nb = (sw * swxy - swx * swy) / det;
+    const double na = (swy - nb * swx) / sw;
+    const double change = std::fabs(na - *a) + std::fabs(nb - *b);
+    *a = na;
+    *b = nb;
+    if (change <= 1e-14 * (std::fabs(na) + std::fabs(nb) + 1e-300)) break;
+  }
+}
+
+}  // namespace
+
+extern "C" int pdd_fit_constants(pdd_problem* p, const pdd_fit_args* a, pdd_fit_out* out) {
+  ProblemView pv;
+  if (!p || !a || !out || !problem_view(p, &pv)) {
+    set_error("pdd_fit_constants: NULL argument");
+    return PDD_ERR_INVALID;
+  }
+  if (a->n_nodes < 1 || a->n_nodes >= ((int64_t)1 << 31) || a->n_h < 2 || a->n_h > 4096 ||
+      !(a->h_min > 0) || !(a->h_max > a->h_min) || !std::isfinite(a->h_max) || a->n_paths < 2 ||
+      !(a->delta > 0) || !(a->q > 0)) {
+    set_error("pdd_fit_constants: bad arguments (need n_nodes >= 1, 2 <= n_h <= 4096, "
+              "0 < h_min < h_max, n_paths >= 2, delta > 0, q > 0)");
+    return PDD_ERR_INVALID;
+  }
+  for (int j = 0; j < pv.dim; ++j)
+    if (!a->coords[j]) {
+      set_error("pdd_fit_constants: coords[%d] is NULL", j);
+      return PDD_ERR_INVALID;
+    }
+  const bool with_psi = a->grid_id != PDD_CV_NONE;
+  const size_t n = (size_t)a->n_nodes, M = (size_t)a->n_h;
+  // per (h, field, node) device statistics: mean_phi, var_phi, mean_steps, cov, var_xi
+  const int kF = 5;
+  if (cudaSetDevice(pv.device) != cudaSuccess) {
+    set_error("pdd_fit_constants: cannot select device %d", pv.device);
+    return PDD_ERR_CUDA;
+  }
+  double* dstat = nullptr;
+  cudaError_t e = cudaMalloc(&dstat, M * kF * n * sizeof(double));
+  if (e != cudaSuccess) {
+    set_error("pdd_fit_constants: cudaMalloc: %s", cudaGetErrorString(e));
+    return PDD_ERR_NOMEM;
+  }
+  std::vector<double> hs(M);
+  for (size_t j = 0; j < M; ++j)
+    hs[j] = a->h_max - (a->h_max - a->h_min) * (double)j / (double)(M - 1);
+  int rc = PDD_OK;
+  for (size_t j0 = 0; j0 < M && rc >= 0; j0 += PDD_MAX_LEVELS) {
+    const size_t nl = std::min<size_t>(PDD_MAX_LEVELS, M - j0);
+    std::vector<pdd_estimate_args> lv(nl);
+    std::vector<pdd_node_stats> os(nl);
+    for (size_t l = 0; l < nl; ++l) {
+      const size_t j = j0 + l;
+      pdd_estimate_args& x = lv[l];
+      x = pdd_estimate_args{};
+      x.n_nodes = a->n_nodes;
+      for (int d = 0; d < 3; ++d) x.coords[d] = a->coords[d];
+      x.coords_on_device = 1;
+      x.grid_id = a->grid_id;
+      x.n_paths = a->n_paths;
+      x.dt = hs[j];
+      x.kappa = 1.0;
+      x.seed = a->seed;
+      x.stream_tag = a->stream_tag_base + (uint32_t)j;
+      pdd_node_stats& o = os[l];
+      o = pdd_node_stats{};
+      o.on_device = 1;
+      double* base = dstat + j * kF * n;
+      o.mean_phi = base;
+      o.var_phi = base + n;
+      o.mean_steps = base + 2 * n;
+      o.cov_phi_xi = base + 3 * n;
+      o.var_xi = base + 4 * n;
+    }
+    rc = pdd_estimate_levels(p, (int)nl, lv.data(), os.data(), 0);
+  }
+  std::vector<double> hstat(M * kF * n);
+  if (rc >= 0) {
+    e = cudaMemcpy(hstat.data(), dstat, hstat.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      set_error("pdd_fit_constants: cudaMemcpy: %s", cudaGetErrorString(e));
+      rc = PDD_ERR_CUDA;
+    }
+  }
+  cudaFree(dstat);
+  if (rc < 0) return rc;
+  std::vector<double> x(M), y(M);
+  for (size_t j = 0; j < M; ++j) x[j] = std::pow(hs[j], a->delta);
+  auto stat = [&](size_t j, int f, size_t i) { return hstat[(j * kF + f) * n + i]; };
+  for (size_t i = 0; i < n; ++i) {
+    double e_phi, beta, v_phi, alpha, e_tau, slope, cov0 = NAN, v_psi = NAN;
+    for (size_t j = 0; j < M; ++j) y[j] = stat(j, 0, i);
+    ols(x, y, &e_phi, &beta);
+    for (size_t j = 0; j < M; ++j) y[j] = stat(j, 2, i) * hs[j];  // tau_h = k h
+    ols(x, y, &e_tau, &slope);
+    for (size_t j = 0; j < M; ++j) y[j] = stat(j, 1, i);
+    gamma_identity(x, y, &v_phi, &alpha);
+    if (with_psi) {
+      for (size_t j = 0; j < M; ++j) y[j] = stat(j, 3, i);  // E[psi phi] = Cov (E psi = 0)
+      ols(x, y, &cov0, &slope);
+      for (size_t j = 0; j < M; ++j) y[j] = stat(j, 4, i);
+      gamma_identity(x, y, &v_psi, &slope);
+    }
+    const double K = 4.0 * a->q * a->q * e_tau * std::pow(2.0 * std::fabs(beta), 1.0 / a->delta);
+    if (out->E_phi) out->E_phi[i] = e_phi;
+    if (out->beta) out->beta[i] = beta;
+    if (out->V_phi) out->V_phi[i] = v_phi;
+    if (out->alpha) out->alpha[i] = alpha;
+    if (out->E_tau) out->E_tau[i] = e_tau;
+    if (out->K) out->K[i] = K;
+    if (out->cov_phi_psi) out->cov_phi_psi[i] = cov0;
+    if (out->V_psi) out->V_psi[i] = v_psi;
+    if (out->rho_phi_psi) out->rho_phi_psi[i] = cov0 / std::sqrt(v_phi * v_psi);
+    if (out->cloud)
+      for (size_t j = 0; j < M; ++j) {
+        double* c = out->cloud + (i * M + j) * 6;
+        c[0] = hs[j];
+        c[1] = stat(j, 0, i);
+        c[2] = stat(j, 1, i);
+        c[3] = stat(j, 2, i) * hs[j];
+        c[4] = stat(j, 3, i);
+        c[5] = stat(j, 4, i);
+      }
+  }
+  return rc;
+}

@@ -16,7 +16,7 @@ constexpr int kAccWords = 16;               // 64-bit words per node record
 static_assert(kAccWords == PDD_RECORD_WORDS, "node record size");
 constexpr unsigned long long kWarpBatch = 32;  // path indices a warp takes per cursor grab
 
-constexpr int kMaxSegments = 32;           // segments (levels / requests) per launch
+constexpr int kMaxSegments = 128;          // segments (levels / requests) per launch
 
 // One segment of a launch: n_nodes x n_paths paths with their own nodes,
 // time step, control grid, random-stream key and output records.

@@ -85,9 +85,14 @@ template <class T, int D, bool MULTI>
 __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long g,
                                            PathState<T>& s, LaneSeg<T>& ls) {
   uint32_t si = 0;
-  if (MULTI) {
-    for (int i = 1; i < a.n_segs; ++i)
-      if (g >= a.seg[i].begin) si = (uint32_t)i;
+  if (MULTI) {  // last segment whose begin <= g (segments in increasing begin)
+    int lo = 0, hi = a.n_segs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.seg[mid].begin <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    si = (uint32_t)lo;
   }
   const SegArgs& sg = a.seg[si];
   const unsigned long long li = g - sg.begin;

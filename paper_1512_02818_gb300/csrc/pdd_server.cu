@@ -428,7 +428,7 @@ int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** ou
   *out = nullptr;
   pdd_server_desc d{};
   if (desc) d = *desc;
-  if (d.max_active <= 0) d.max_active = kMaxSegments;
+  if (d.max_active <= 0) d.max_active = 32;
   if (d.max_active > kMaxSegments) {
     set_error("pdd_server_create: max_active %d > %d", d.max_active, kMaxSegments);
     return PDD_ERR_INVALID;

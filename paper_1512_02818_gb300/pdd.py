@@ -30,7 +30,7 @@ PDD_DTYPE_F32, PDD_DTYPE_F64 = 0, 1
 PDD_CV_NONE, PDD_CV_EXACT = -1, -2
 PDD_MAX_GRIDS = 8
 PDD_FLAG_EMIT_PATHS, PDD_FLAG_ASYNC, PDD_FLAG_GRAPH = 1, 2, 4
-PDD_MAX_LEVELS = 32
+PDD_MAX_LEVELS = 128
 PDD_RECORD_WORDS = 16
 
 STAT_FIELDS = ["mean_phi", "var_phi", "mean_cv", "var_cv", "cov_phi_xi", "var_xi", "rho",
@@ -67,6 +67,22 @@ class EstimateArgs(ctypes.Structure):
 class NodeStats(ctypes.Structure):
     _fields_ = ([("on_device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
                 + [(f, ctypes.c_void_p) for f in STAT_FIELDS + COUNT_FIELDS])
+
+
+class FitArgs(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("coords", ctypes.c_void_p * 3),
+                ("grid_id", ctypes.c_int32), ("n_h", ctypes.c_int32), ("h_min", ctypes.c_double),
+                ("h_max", ctypes.c_double), ("n_paths", ctypes.c_int64),
+                ("delta", ctypes.c_double), ("q", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("stream_tag_base", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+FIT_FIELDS = ["E_phi", "beta", "V_phi", "alpha", "E_tau", "K", "cov_phi_psi", "V_psi",
+              "rho_phi_psi"]
+
+
+class FitOut(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_void_p) for f in FIT_FIELDS] + [("cloud", ctypes.c_void_p)]
 
 
 class ServerDesc(ctypes.Structure):
@@ -119,6 +135,8 @@ _SIGS = [
     ("pdd_finalize_records", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.c_double, ctypes.POINTER(NodeStats)]),
     ("pdd_records_merge", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    ("pdd_fit_constants", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(FitArgs),
+                                         ctypes.POINTER(FitOut)]),
     ("pdd_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerDesc),
                                          ctypes.POINTER(ctypes.c_void_p)]),
     ("pdd_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
@@ -262,6 +280,10 @@ def pdd_finalize_records(ctx: int, records_ptr: int, n_nodes: int, kappa: float,
 
 def pdd_records_merge(dst_ptr: int, src_ptr: int, n_nodes: int) -> None:
     _check(lib().pdd_records_merge(dst_ptr, src_ptr, n_nodes))
+
+
+def pdd_fit_constants(problem: int, args: FitArgs, out: FitOut) -> int:
+    return _check(lib().pdd_fit_constants(problem, ctypes.byref(args), ctypes.byref(out)))
 
 
 def pdd_server_create(ctx: int, desc: ServerDesc | None = None) -> int:
@@ -511,6 +533,33 @@ class Problem:
         args, _, keep = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, 1.0, False,
                                       True, False, False)
         return pdd_accumulate(self.handle, args, path_offset, records.data_ptr())
+
+    def fit_constants(self, nodes, n_paths: int, h_min: float, h_max: float, n_h: int,
+                      grid_id: int = PDD_CV_NONE, delta: float = 1.0, q: float = 2.0,
+                      seed: int = 1234, stream_tag_base: int = 0):
+        """Algorithm 3 on the GPU; returns a dict of per-node numpy arrays and
+        the cloud (n_nodes, n_h, 6)."""
+        import numpy as np
+        torch = _torch()
+        dev = torch.device("cuda", self.ctx.device)
+        nodes = np.asarray(nodes, dtype=np.float32).reshape(-1, self.dim)
+        cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).to(dev)
+                for j in range(self.dim)]
+        n = nodes.shape[0]
+        a = FitArgs()
+        a.n_nodes = n
+        for j in range(3):
+            a.coords[j] = cols[j].data_ptr() if j < self.dim else None
+        a.grid_id, a.n_h, a.h_min, a.h_max = grid_id, n_h, h_min, h_max
+        a.n_paths, a.delta, a.q, a.seed, a.stream_tag_base = n_paths, delta, q, seed, stream_tag_base
+        res = {f: np.zeros(n) for f in FIT_FIELDS}
+        res["cloud"] = np.zeros((n, n_h, 6))
+        out = FitOut()
+        for f in FIT_FIELDS + ["cloud"]:
+            setattr(out, f, res[f].ctypes.data)
+        torch.cuda.synchronize()
+        res["status"] = pdd_fit_constants(self.handle, a, out)
+        return res
 
     def autotune(self, nodes, n_paths: int, dt: float, grid_id: int = PDD_CV_NONE,
                  seed: int = 1234, stream_tag: int = 0):

@@ -1,0 +1,48 @@
+"""Fast fit of nodal constants (Algorithm 3) on the GPU against the oracle's
+fit on the same random streams: the clouds agree within the path tolerance
+and the fitted constants within what those differences allow."""
+import numpy as np
+import pytest
+
+from paper_1512_02818_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fit_constants_match_oracle():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    from paper_1512_02818_gb300 import build, pdd
+    build.build()
+    oracle.build()
+    ctx = pdd.Context(0)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    # synthetic error-propagation function w = sin(3 pi x) sin(2 pi y), zero on the boundary
+    wg = W.control_grid(0, 65, 1.0) - W.control_grid(0, 65, 0.0)
+    prob.set_control_grid(0, wg)
+    nodes = W.workload_nodes("c0")[::4]
+    kw = dict(n_paths=400, h_min=2e-3, h_max=1e-2, n_h=6, delta=1.0, q=2.0, seed=31)
+    g = prob.fit_constants(nodes, grid_id=0, stream_tag_base=100, **kw)
+    o = oracle.fit_constants(0, nodes, kw["n_paths"], kw["h_min"], kw["h_max"], kw["n_h"],
+                             delta=1.0, q=2.0, seed=31, tag_base=100, cv=oracle.CV_GRID,
+                             grad=oracle.build_gradient(2, wg), grid_n=65)
+    assert g["status"] == 0
+    assert np.allclose(g["cloud"][:, :, 0], o["cloud"][:, :, 0], rtol=0, atol=0)
+    # cloud: means within a few 1e-5 (FP32 paths, rare exit-step flips)
+    for col, tol in ((1, 2e-3), (3, 1e-5), (4, 2e-3)):
+        assert np.allclose(g["cloud"][:, :, col], o["cloud"][:, :, col], atol=tol), col
+    for col in (2, 5):
+        assert np.allclose(g["cloud"][:, :, col], o["cloud"][:, :, col], rtol=2e-2), col
+    # fits are linear (or nearly) in the cloud: same constants up to those differences
+    assert np.allclose(g["E_phi"], o["E_phi"], atol=5e-3)
+    assert np.allclose(g["E_tau"], o["E_tau"], atol=1e-4)
+    assert np.allclose(g["V_phi"], o["V_phi"], rtol=3e-2)
+    assert np.allclose(g["V_psi"], o["V_psi"], rtol=3e-2)
+    assert np.allclose(g["rho_phi_psi"], o["rho_phi_psi"], atol=2e-2)
+    assert np.all(np.isfinite(g["K"])) and np.all(g["K"] > 0)
+    with pytest.raises(pdd.PddError):
+        prob.fit_constants(nodes, n_paths=10, h_min=1e-2, h_max=1e-3, n_h=4)
+    prob.close()
+    ctx.close()
