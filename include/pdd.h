@@ -291,6 +291,30 @@ typedef struct {
 
 int pdd_fit_constants(pdd_problem* problem, const pdd_fit_args* args, pdd_fit_out* out);
 
+/* Scheduling of the tolerance sequence (Algorithm 4, with the sensitivity
+   formula eq. F:Sensitivity_formula).  Host computation, no GPU.  Inputs per
+   node i (arrays of n_nodes): K_i, beta_i, alpha_i, V_i[phi], V_i[psi],
+   rho_i[phi, psi] (as fitted by pdd_fit_constants), and delta, kappa and the
+   nodal target tolerance a0.  Step j solves
+     a_{j+1} = argmin_{a > a_j} sum_i K_i V_i[phi] ( kappa (1 - r_i^2(a)
+               + |alpha_i r_i(a) / beta_i| a_j) + (a_j / a)^{2 + 1/delta} ),
+     r_i^2(a) = 1 - V_i[psi] a^2 (1 - rho_i^2) / (4 V_i[phi])  (clamped at 0),
+   by a log-spaced scan and golden-section refinement on (a_j, a_max], a_max
+   the largest a with some r_i^2 > 0, and stops when the predicted speedup
+   S_j = sum_i K_i V_i[phi] / (minimum value) falls below min_speedup (the
+   paper stops at 1.5) or after max_levels levels.  Outputs: a[0] = a0,
+   a[1..J] the coarser tolerances (a has room for max_levels + 1 values),
+   speedup[j] = S_j of step j (speedup[J] is the rejected step's, NaN when
+   no step was tried; room for max_levels + 1 values); *n_levels = J.        */
+typedef struct {
+  int64_t n_nodes;
+  const double *K, *beta, *alpha, *V_phi, *V_psi, *rho_phi_psi;
+  double delta, kappa, a0, min_speedup;
+} pdd_schedule_args;
+
+int pdd_schedule(const pdd_schedule_args* args, double* a, double* speedup, int max_levels,
+                 int* n_levels);
+
 /* Autotuner: runs `sample` (device coordinates) under candidate launch shapes
    (128/256/512 threads per block, full and half occupancy), times each with
    CUDA events on the context's stream, and keeps the fastest as the context's

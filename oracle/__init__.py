@@ -339,3 +339,48 @@ def fit_constants(kind, nodes, n_paths, h_min, h_max, n_h, delta=1.0, q=2.0, see
         out["K"][i] = 4 * q * q * out["E_tau"][i] * (2 * abs(out["beta"][i])) ** (1 / delta)
     out["cloud"] = cloud
     return out
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 4 (scheduling) with the sensitivity formula, plain numpy/scipy.
+# ---------------------------------------------------------------------------
+def schedule_cost(a, aj, K, beta, alpha, V_phi, V_psi, rho, delta, kappa):
+    """Predicted cost of the level with tolerance aj when the control variate
+    comes from the coarser level with tolerance a (Algorithm 4's objective)."""
+    r2 = 1.0 - V_psi * a * a * (1.0 - rho * rho) / (4.0 * V_phi)
+    r2 = np.maximum(r2, 0.0)
+    r = np.sqrt(r2)
+    p = 2.0 + 1.0 / delta
+    return float(np.sum(K * V_phi * (kappa * (1.0 - r2 + np.abs(alpha * r / beta) * aj)
+                                     + (aj / a) ** p)))
+
+
+def schedule(K, beta, alpha, V_phi, V_psi, rho, delta, kappa, a0, min_speedup=1.5,
+             max_levels=20):
+    """Tolerance sequence a0 < a1 < ... and the predicted speedup of each
+    step; stops when the predicted speedup drops below min_speedup."""
+    from scipy import optimize
+    K, beta, alpha, V_phi, V_psi, rho = (np.asarray(v, dtype=np.float64)
+                                         for v in (K, beta, alpha, V_phi, V_psi, rho))
+    plain = float(np.sum(K * V_phi))
+    c = V_psi * (1 - rho * rho) / (4 * V_phi)
+    amax = float(np.max(1 / np.sqrt(c[c > 0])))
+    seq, sp = [a0], []
+    aj = a0
+    while len(seq) - 1 < max_levels and aj < amax:
+        f = lambda la: schedule_cost(np.exp(la), aj, K, beta, alpha, V_phi, V_psi, rho, delta,
+                                     kappa)
+        grid = np.linspace(np.log(aj), np.log(amax), 4001)[1:]
+        vals = np.array([f(g) for g in grid])
+        k = int(np.argmin(vals))
+        lo, hi = grid[max(k - 1, 0)], grid[min(k + 1, len(grid) - 1)]
+        res = optimize.minimize_scalar(f, bounds=(lo, hi), method="bounded",
+                                       options=dict(xatol=1e-12))
+        best = res.x if res.fun <= vals[k] else grid[k]
+        S = plain / min(res.fun, vals[k])
+        sp.append(S)
+        if S < min_speedup:
+            break
+        aj = float(np.exp(best))
+        seq.append(aj)
+    return np.array(seq), np.array(sp)

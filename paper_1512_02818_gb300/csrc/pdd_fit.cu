@@ -190,3 +190,98 @@ extern "C" int pdd_fit_constants(pdd_problem* p, const pdd_fit_args* a, pdd_fit_
   }
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// Algorithm 4: scheduling of the tolerance sequence a_J > ... > a_1 > a_0.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SchedData {
+  const pdd_schedule_args* a;
+  double p;  // 2 + 1/delta
+};
+
+// Predicted cost of the level with tolerance aj using the control variate of
+// the coarser level with tolerance a (the minimised objective of Algorithm 4).
+double sched_cost(const SchedData& d, double a, double aj) {
+  const pdd_schedule_args& s = *d.a;
+  double tot = 0.0;
+  for (int64_t i = 0; i < s.n_nodes; ++i) {
+    double r2 = 1.0 - s.V_psi[i] * a * a * (1.0 - s.rho_phi_psi[i] * s.rho_phi_psi[i]) /
+                          (4.0 * s.V_phi[i]);
+    if (r2 < 0.0) r2 = 0.0;
+    const double r = std::sqrt(r2);
+    const double vr = 1.0 - r2 + std::fabs(s.alpha[i] * r / s.beta[i]) * aj;
+    tot += s.K[i] * s.V_phi[i] * (s.kappa * vr + std::pow(aj / a, d.p));
+  }
+  return tot;
+}
+
+}  // namespace
+
+extern "C" int pdd_schedule(const pdd_schedule_args* s, double* a, double* speedup,
+                            int max_levels, int* n_levels) {
+  if (!s || !a || !n_levels || max_levels < 1 || s->n_nodes < 1 || !s->K || !s->beta ||
+      !s->alpha || !s->V_phi || !s->V_psi || !s->rho_phi_psi || !(s->delta > 0) ||
+      !(s->kappa > 0) || !(s->a0 > 0)) {
+    set_error("pdd_schedule: bad arguments");
+    return PDD_ERR_INVALID;
+  }
+  SchedData d{s, 2.0 + 1.0 / s->delta};
+  double plain = 0.0, amax = 0.0;
+  for (int64_t i = 0; i < s->n_nodes; ++i) {
+    plain += s->K[i] * s->V_phi[i];
+    const double c = s->V_psi[i] * (1.0 - s->rho_phi_psi[i] * s->rho_phi_psi[i]) /
+                     (4.0 * s->V_phi[i]);
+    if (c > 0) amax = std::max(amax, 1.0 / std::sqrt(c));
+  }
+  const double min_s = s->min_speedup > 0 ? s->min_speedup : 1.5;
+  a[0] = s->a0;
+  int J = 0;
+  double aj = s->a0;
+  if (speedup)
+    for (int k = 0; k <= max_levels; ++k) speedup[k] = NAN;  // steps not taken
+  while (J < max_levels && aj < amax) {
+    // log-spaced scan of (aj, amax], then golden-section refinement
+    const int kScan = 2000;
+    const double l0 = std::log(aj), l1 = std::log(amax);
+    int best = 1;
+    double bestv = 1e300;
+    for (int k = 1; k <= kScan; ++k) {
+      const double v = sched_cost(d, std::exp(l0 + (l1 - l0) * k / kScan), aj);
+      if (v < bestv) {
+        bestv = v;
+        best = k;
+      }
+    }
+    double lo = l0 + (l1 - l0) * (best - 1) / kScan, hi = l0 + (l1 - l0) * std::min(best + 1, kScan) / kScan;
+    const double g = 0.5 * (std::sqrt(5.0) - 1.0);
+    double x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+    double f1 = sched_cost(d, std::exp(x1), aj), f2 = sched_cost(d, std::exp(x2), aj);
+    for (int it = 0; it < 200 && hi - lo > 1e-14; ++it) {
+      if (f1 < f2) {
+        hi = x2;
+        x2 = x1;
+        f2 = f1;
+        x1 = hi - g * (hi - lo);
+        f1 = sched_cost(d, std::exp(x1), aj);
+      } else {
+        lo = x1;
+        x1 = x2;
+        f1 = f2;
+        x2 = lo + g * (hi - lo);
+        f2 = sched_cost(d, std::exp(x2), aj);
+      }
+    }
+    const double xbest = f1 < f2 ? x1 : x2;
+    const double fbest = std::min(f1, f2);
+    const double S = plain / std::min(fbest, bestv);
+    const double anext = fbest <= bestv ? std::exp(xbest) : std::exp(l0 + (l1 - l0) * best / kScan);
+    if (speedup) speedup[J] = S;
+    if (S < min_s) break;
+    a[++J] = anext;
+    aj = anext;
+  }
+  *n_levels = J;
+  return PDD_OK;
+}

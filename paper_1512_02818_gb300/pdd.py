@@ -85,6 +85,12 @@ class FitOut(ctypes.Structure):
     _fields_ = [(f, ctypes.c_void_p) for f in FIT_FIELDS] + [("cloud", ctypes.c_void_p)]
 
 
+class ScheduleArgs(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64)] + [(f, ctypes.c_void_p) for f in
+                ("K", "beta", "alpha", "V_phi", "V_psi", "rho_phi_psi")] + [
+                (f, ctypes.c_double) for f in ("delta", "kappa", "a0", "min_speedup")]
+
+
 class ServerDesc(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("max_queue", ctypes.c_int32),
                 ("quantum_path_steps", ctypes.c_int64), ("device_arena_bytes", ctypes.c_size_t)]
@@ -137,6 +143,8 @@ _SIGS = [
     ("pdd_records_merge", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     ("pdd_fit_constants", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(FitArgs),
                                          ctypes.POINTER(FitOut)]),
+    ("pdd_schedule", ctypes.c_int, [ctypes.POINTER(ScheduleArgs), ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("pdd_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerDesc),
                                          ctypes.POINTER(ctypes.c_void_p)]),
     ("pdd_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
@@ -284,6 +292,24 @@ def pdd_records_merge(dst_ptr: int, src_ptr: int, n_nodes: int) -> None:
 
 def pdd_fit_constants(problem: int, args: FitArgs, out: FitOut) -> int:
     return _check(lib().pdd_fit_constants(problem, ctypes.byref(args), ctypes.byref(out)))
+
+
+def pdd_schedule(K, beta, alpha, V_phi, V_psi, rho, delta: float, kappa: float, a0: float,
+                 min_speedup: float = 1.5, max_levels: int = 20):
+    """Algorithm 4 (host computation in the library): returns (a, speedup)
+    with a[0] = a0 < a[1] < ... and the predicted speedup of every step."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (K, beta, alpha, V_phi, V_psi, rho)]
+    args = ScheduleArgs(arrs[0].size, *[x.ctypes.data for x in arrs], delta, kappa, a0,
+                        min_speedup)
+    a = np.zeros(max_levels + 1)
+    sp = np.zeros(max_levels + 1)
+    n = ctypes.c_int()
+    _check(lib().pdd_schedule(ctypes.byref(args), a.ctypes.data, sp.ctypes.data, max_levels,
+                              ctypes.byref(n)))
+    J = n.value
+    n_sp = J + 1 if J < max_levels else J
+    return a[: J + 1].copy(), sp[:n_sp].copy()
 
 
 def pdd_server_create(ctx: int, desc: ServerDesc | None = None) -> int:
