@@ -79,7 +79,11 @@ typedef enum {
   /* D=3, b = 0, c = 1, sigma = I, u = e^x sin y cos z + x y z.            */
   PDD_PROBLEM_CUBE_3D = 2,
   /* D=2, b = c = f = 0, sigma = I, g = u = x^2 - y^2 (harmonic).          */
-  PDD_PROBLEM_HARMONIC_2D = 3
+  PDD_PROBLEM_HARMONIC_2D = 3,
+  /* D=2, the paper's example (Sec. 6, eq. F:PDE_ejemplo): sigma = sqrt(2) I,
+     b = cos(x+y) [1,1] / (1.1 + sin(x+y)), c = (x^2+y^2) / (1.1 + sin(x+y)),
+     u = 2 cos(2 (y-2) x) + sin(3 (x-2) y) + 3.1, f from the PDE, g = u.   */
+  PDD_PROBLEM_PAPER_EX_2D = 4
 } pdd_problem_kind;
 
 typedef enum {
@@ -253,6 +257,22 @@ int pdd_accumulate(pdd_problem* problem, const pdd_estimate_args* args, uint64_t
 int pdd_finalize_records(pdd_ctx* ctx, const uint64_t* records, int64_t n_nodes, double kappa,
                          pdd_node_stats* out);
 int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes);
+
+/* Multilevel coupling (the multilevel Monte Carlo variant the paper names as
+   future work, Sec. 1 and Sec. 7), 2D problems with FP32 paths.  For every
+   (node, path) the library runs a FINE path at h/2 = args->dt / 2 on the
+   path's own random stream (the same path pdd_estimate_nodes runs at dt/2)
+   and a COARSE path at h = args->dt driven by the sums of pairs of fine
+   increments, dW_c(k) = dW_f(2k) + dW_f(2k+1); each path has its own exit.
+   out_fine receives the statistics of the fine level (as pdd_estimate_nodes
+   at dt/2); out_diff those of the level difference: mean_phi / var_phi of
+   phi_f - phi_c, mean_cv / var_cv of (phi_f + xi_f) - (phi_c + xi_c),
+   mean_steps of the coarse path.  The difference has a small variance, so
+   E[phi_h/2] - E[phi_h] is cheap to resolve (the multilevel telescoping sum).
+   Coordinates and outputs are device pointers; with PDD_FLAG_EMIT_PATHS the
+   per-path arrays hold 2 x n_nodes x n_paths entries, fine first.          */
+int pdd_estimate_coupled(pdd_problem* problem, const pdd_estimate_args* args,
+                         pdd_node_stats* out_fine, pdd_node_stats* out_diff);
 
 /* Fast fit of nodal constants (Algorithm 3, Sec. 5 H5).  For every node the
    library runs n_paths realisations of Algorithm 1 at each of n_h equispaced

@@ -29,7 +29,7 @@ _lib = None
 
 # problem kinds (same numbering as the library's public enum, by definition of
 # the workloads, not by shared code)
-CFG0_2D, ANISO_2D, CUBE_3D, HARMONIC_2D = 0, 1, 2, 3
+CFG0_2D, ANISO_2D, CUBE_3D, HARMONIC_2D, PAPER_EX_2D = 0, 1, 2, 3, 4
 CV_NONE, CV_GRID, CV_EXACT = 0, 1, 2
 GOBET_MENOZZI_C0 = 0.5826  # Algorithm 1, shrinkage constant as printed
 
@@ -84,6 +84,9 @@ def _load():
         lib.or_sample_paths.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, P, P, P,
                                         dbl, u64, u32, P, P, P]
         lib.or_sample_paths.restype = i32
+        lib.or_coupled_paths.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, i64, dbl, u64,
+                                         u32, P, P, P, P, P, P]
+        lib.or_coupled_paths.restype = i32
         assert lib.or_nstat() == len(STAT_NAMES)
         _lib = lib
         return lib
@@ -384,3 +387,30 @@ def schedule(K, beta, alpha, V_phi, V_psi, rho, delta, kappa, a0, min_speedup=1.
         aj = float(np.exp(best))
         seq.append(aj)
     return np.array(seq), np.array(sp)
+
+
+def coupled_paths(kind, nodes, n_paths, h, seed=1234, tag=0, cv=CV_NONE, grad=None, grid_n=0,
+                  c0=GOBET_MENOZZI_C0, y_exp=False, max_steps=None):
+    """Multilevel coupling: per (node, path) the fine path at h/2 (own normal
+    stream) and the coarse path at h driven by the sums of pairs of fine
+    increments.  Returns per-path arrays (n_nodes, n_paths)."""
+    lib = _load()
+    nodes = np.asarray(nodes, dtype=np.float64).reshape(-1, 2)
+    n = nodes.shape[0]
+    xs = np.ascontiguousarray(nodes[:, 0])
+    ys = np.ascontiguousarray(nodes[:, 1])
+    if max_steps is None:
+        max_steps = default_max_steps(0.5 * h)
+    tot = n * n_paths
+    out = {k: np.zeros(tot) for k in ("phi_f", "xi_f", "phi_c", "xi_c")}
+    out["steps_f"] = np.zeros(tot, dtype=np.int64)
+    out["steps_c"] = np.zeros(tot, dtype=np.int64)
+    if grad is not None:
+        grad = np.ascontiguousarray(grad, dtype=np.float64)
+    rc = lib.or_coupled_paths(kind, c0, int(y_exp), int(max_steps), cv, grid_n, _ptr(grad), n,
+                              _ptr(xs), _ptr(ys), int(n_paths), float(h), int(seed), int(tag),
+                              _ptr(out["phi_f"]), _ptr(out["xi_f"]), _ptr(out["steps_f"]),
+                              _ptr(out["phi_c"]), _ptr(out["xi_c"]), _ptr(out["steps_c"]))
+    if rc != 0:
+        raise RuntimeError("or_coupled_paths failed")
+    return {k: v.reshape(n, n_paths) for k, v in out.items()}

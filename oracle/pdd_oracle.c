@@ -103,7 +103,7 @@ double or_normal(uint64_t seed, uint32_t tag, uint32_t node, uint32_t path, uint
 /* sigma sigma^T = A (lower Cholesky factor, Sec. 2.1), the Dirichlet data   */
 /* g = u and the analytic gradient of u.                                     */
 /* ------------------------------------------------------------------------ */
-enum { OR_CFG0_2D = 0, OR_ANISO_2D = 1, OR_CUBE_3D = 2, OR_HARMONIC_2D = 3 };
+enum { OR_CFG0_2D = 0, OR_ANISO_2D = 1, OR_CUBE_3D = 2, OR_HARMONIC_2D = 3, OR_PAPER_EX_2D = 4 };
 
 int or_problem_dim(int kind) { return kind == OR_CUBE_3D ? 3 : 2; }
 
@@ -162,6 +162,25 @@ void or_eval(int kind, const double* x, or_coeffs* o) {
     /* Delta u = -e^x sin y cos z (the xyz term is harmonic). */
     double lap = -ex * sy * cz;
     o->f = 0.5 * lap - o->c * o->u;
+  } else if (kind == OR_PAPER_EX_2D) {
+    /* The paper's example (Sec. 6): Laplacian + b.grad u - c u + f = 0 with
+       sigma = sqrt(2) I (A = 2I), b = cos(x+y) [1,1] / (1.1 + sin(x+y)),
+       c = (x^2 + y^2) / (1.1 + sin(x+y)) and exact
+       u = 2 cos(2 (y-2) x) + sin(3 (x-2) y) + 3.1.  In the form
+       1/2 sum a_ij u_ij + b.grad u - c u = f used here, f = -(the paper's f). */
+    double x0 = x[0], y0 = x[1];
+    double p = 2.0 * x0 * (y0 - 2.0), q = 3.0 * y0 * (x0 - 2.0);
+    o->u = 2.0 * cos(p) + sin(q) + 3.1;
+    o->grad_u[0] = -4.0 * (y0 - 2.0) * sin(p) + 3.0 * y0 * cos(q);
+    o->grad_u[1] = -4.0 * x0 * sin(p) + 3.0 * (x0 - 2.0) * cos(q);
+    double lap = -8.0 * ((y0 - 2.0) * (y0 - 2.0) + x0 * x0) * cos(p) -
+                 9.0 * (y0 * y0 + (x0 - 2.0) * (x0 - 2.0)) * sin(q);
+    double den = 1.1 + sin(x0 + y0);
+    o->b[0] = o->b[1] = cos(x0 + y0) / den;
+    o->c = (x0 * x0 + y0 * y0) / den;
+    o->A[0][0] = o->A[1][1] = 2.0;
+    o->sigma[0][0] = o->sigma[1][1] = sqrt(2.0);
+    o->f = lap + o->b[0] * o->grad_u[0] + o->b[1] * o->grad_u[1] - o->c * o->u;
   } else { /* OR_HARMONIC_2D: b = c = f = 0, sigma = I, u = x^2 - y^2 */
     o->u = x[0] * x[0] - x[1] * x[1];
     o->grad_u[0] = 2.0 * x[0];
@@ -362,6 +381,94 @@ void or_simulate_path(const or_problem* pb, const double* x0, double h, uint64_t
   for (int j = 0; j < 3; ++j) { res->x_stop[j] = X[j]; res->x_exit[j] = P[j]; }
   res->steps = k;
   res->truncated = trunc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multilevel coupling (the multilevel Monte Carlo variant the paper names as */
+/* future work): the fine path runs Algorithm 1 at h/2 on the path's own      */
+/* normal stream; the coarse path runs it at h with increment                  */
+/* dW_c(k) = dW_f(2k) + dW_f(2k+1), i.e. normals (n(2k) + n(2k+1)) / sqrt(2)   */
+/* per component.  Each path has its own exit.                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double phi_f, xi_f, phi_c, xi_c;
+  int64_t steps_f, steps_c;
+} or_coupled;
+
+static void or_run_path(const or_problem* pb, const double* x0, double h, uint64_t seed,
+                        uint32_t tag, uint32_t node, uint32_t path, int coarse, or_path* res) {
+  int dim = or_problem_dim(pb->kind);
+  double X[3] = {0, 0, 0};
+  for (int j = 0; j < dim; ++j) X[j] = x0[j];
+  double Y = 1.0, Z = 0.0, xi = 0.0;
+  double sqh = sqrt(h);
+  int64_t k = 0;
+  int trunc = 0;
+  or_coeffs o;
+  for (;;) {
+    int axis = 0, side = 0;
+    double d = or_box_distance(dim, X, &axis, &side);
+    or_eval(pb->kind, X, &o);
+    double s = sqrt(o.A[axis][axis]);
+    if (d >= -pb->c0 * s * sqh) break;
+    double n[3], dW[3], sdW[3] = {0, 0, 0};
+    for (int j = 0; j < dim; ++j) {
+      if (coarse) {
+        double a = or_normal(seed, tag, node, path, (uint64_t)dim * (uint64_t)(2 * k) + (uint64_t)j);
+        double b = or_normal(seed, tag, node, path, (uint64_t)dim * (uint64_t)(2 * k + 1) + (uint64_t)j);
+        n[j] = (a + b) / sqrt(2.0);
+      } else {
+        n[j] = or_normal(seed, tag, node, path, (uint64_t)dim * (uint64_t)k + (uint64_t)j);
+      }
+      dW[j] = sqh * n[j];
+    }
+    for (int i = 0; i < dim; ++i)
+      for (int j = 0; j <= i; ++j) sdW[i] += o.sigma[i][j] * dW[j];
+    if (pb->cv_mode != OR_CV_NONE) {
+      double gv[3] = {0, 0, 0};
+      if (pb->cv_mode == OR_CV_GRID) or_grad_interp(dim, pb->grid_n, pb->grad, X, gv);
+      else for (int j = 0; j < dim; ++j) gv[j] = o.grad_u[j];
+      double dot = 0.0;
+      for (int i = 0; i < dim; ++i) dot += gv[i] * sdW[i];
+      xi -= Y * dot;
+    }
+    Z -= h * Y * o.f;
+    for (int j = 0; j < dim; ++j) X[j] += h * o.b[j] + sdW[j];
+    Y *= pb->y_exp ? exp(-h * o.c) : (1.0 - h * o.c);
+    k += 1;
+    if (k >= pb->max_steps) { trunc = 1; break; }
+  }
+  double P[3] = {0, 0, 0};
+  or_box_project(dim, X, P);
+  or_coeffs oe;
+  or_eval(pb->kind, P, &oe);
+  res->phi = oe.u * Y + Z;
+  res->xi = xi;
+  res->steps = k;
+  res->truncated = trunc;
+}
+
+/* Coupled pairs for n_nodes x n_paths; h is the COARSE step (fine: h/2).    */
+/* Per-path outputs indexed node * n_paths + path; max_steps caps each path. */
+int or_coupled_paths(int kind, double c0, int y_exp, int64_t max_steps, int cv_mode, int grid_n,
+                     const double* grad, int64_t n_nodes, const double* xs, const double* ys,
+                     int64_t n_paths, double h, uint64_t seed, uint32_t tag, double* phi_f,
+                     double* xi_f, int64_t* steps_f, double* phi_c, double* xi_c,
+                     int64_t* steps_c) {
+  or_problem pb = {kind, c0, y_exp, max_steps, cv_mode, grid_n, grad};
+  if (or_problem_dim(kind) != 2) return -1;
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    double x0[3] = {xs[i], ys[i], 0.0};
+    for (int64_t p = 0; p < n_paths; ++p) {
+      or_path f, c;
+      or_run_path(&pb, x0, 0.5 * h, seed, tag, (uint32_t)i, (uint32_t)p, 0, &f);
+      or_run_path(&pb, x0, h, seed, tag, (uint32_t)i, (uint32_t)p, 1, &c);
+      int64_t q = i * n_paths + p;
+      phi_f[q] = f.phi; xi_f[q] = f.xi; steps_f[q] = f.steps;
+      phi_c[q] = c.phi; xi_c[q] = c.xi; steps_c[q] = c.steps;
+    }
+  }
+  return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -672,7 +672,7 @@ int pdd_create_problem(pdd_ctx* c, const pdd_problem_desc* d, pdd_problem** out)
     return PDD_ERR_INVALID;
   }
   *out = nullptr;
-  if (d->kind < PDD_PROBLEM_CFG0_2D || d->kind > PDD_PROBLEM_HARMONIC_2D) {
+  if (d->kind < PDD_PROBLEM_CFG0_2D || d->kind > PDD_PROBLEM_PAPER_EX_2D) {
     set_error("pdd_create_problem: unknown problem kind %d", d->kind);
     return PDD_ERR_INVALID;
   }
@@ -964,6 +964,110 @@ int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes) {
     }
     a[14] += b[14];
     a[15] += b[15];
+  }
+  return PDD_OK;
+}
+
+int pdd_estimate_coupled(pdd_problem* p, const pdd_estimate_args* a, pdd_node_stats* out_fine,
+                         pdd_node_stats* out_diff) {
+  if (!p || !a || !out_fine || !out_diff) {
+    set_error("pdd_estimate_coupled: NULL argument");
+    return PDD_ERR_INVALID;
+  }
+  if (p->dim != 2 || p->desc.precision != PDD_PATH_FP32) {
+    set_error("pdd_estimate_coupled: provided for 2D problems with FP32 paths");
+    return PDD_ERR_INVALID;
+  }
+  LevelPlan lp;
+  int rc = check_level(p, a, out_fine, "pdd_estimate_coupled", 0, &lp);
+  if (rc != PDD_OK) return rc;
+  if (!a->coords_on_device || !out_fine->on_device || !out_diff->on_device) {
+    set_error("pdd_estimate_coupled: coordinates and outputs must be device pointers");
+    return PDD_ERR_INVALID;
+  }
+  if (a->n_nodes == 0) return PDD_OK;
+  const double hf = 0.5 * a->dt, hc = a->dt;
+  auto steps_cap = [&](double h) -> int {
+    int64_t ms = p->desc.max_steps;
+    if (ms <= 0) ms = (int64_t)std::min(2.0e9, std::ceil(100.0 / h));
+    return (int)std::min<int64_t>(ms, 2000000000ll);
+  };
+  pdd_ctx* c = p->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const size_t n = (size_t)a->n_nodes;
+  const size_t rec_bytes = n * kAccWords * 8;
+  rc = ensure_workspace(c, 256 + 2 * align_up(rec_bytes, 256));
+  if (rc != PDD_OK) return rc;
+  char* ws = (char*)c->ws;
+  WsHeader* hdr = (WsHeader*)ws;
+  unsigned long long* rf = (unsigned long long*)(ws + 256);
+  unsigned long long* rd = (unsigned long long*)(ws + 256 + align_up(rec_bytes, 256));
+  PathArgs pa{};
+  pa.cursor = &hdr->cursor;
+  pa.err = &hdr->err;
+  pa.trunc_total = &hdr->trunc_total;
+  pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
+  pa.max_blocks = c->max_blocks;
+  pa.block_threads = c->block_threads;
+  pa.n_segs = 2;
+  pa.total = (unsigned long long)n * (unsigned long long)a->n_paths;
+  const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
+  const bool emit = (a->flags & PDD_FLAG_EMIT_PATHS) != 0;
+  for (int l = 0; l < 2; ++l) {
+    SegArgs& sg = pa.seg[l];
+    const double h = l == 0 ? hf : hc;
+    sg.cx = a->coords[0];
+    sg.cy = a->coords[1];
+    sg.cz = a->coords[0];
+    sg.begin = 0;
+    sg.total = pa.total;
+    sg.n_paths = (unsigned long long)a->n_paths;
+    sg.acc = l == 0 ? rf : rd;
+    sg.grad = lp.table;
+    const size_t off = l == 0 ? 0 : n * (size_t)a->n_paths;
+    sg.emit_phi = emit ? a->path_phi + off : nullptr;
+    sg.emit_xi = emit ? a->path_xi + off : nullptr;
+    sg.emit_steps = emit ? a->path_steps + off : nullptr;
+    sg.emit_stride = (unsigned long long)a->n_paths;
+    sg.h = h;
+    sg.sqrt_h = std::sqrt(h);
+    sg.thr0 = c0 * sg.sqrt_h;
+    sg.path_off = 0;
+    sg.key0 = (uint32_t)a->seed;
+    sg.key1 = a->stream_tag;
+    sg.seed_hi = (uint32_t)(a->seed >> 32);
+    sg.grid_n = lp.grid_n;
+    sg.max_steps = steps_cap(h);
+  }
+  PDD_CUDA(cudaMemsetAsync(ws, 0, 256 + 2 * align_up(rec_bytes, 256), c->stream),
+           "cudaMemsetAsync");
+  int blocks = 0;
+  PDD_CUDA(launch_coupled(p->desc.kind, lp.cv, pa, c->num_sms, c->stream, &blocks),
+           "coupled kernel launch");
+  const double kappa = a->kappa > 0.0 ? a->kappa : 1.0;
+  pdd_node_stats* outs[2] = {out_fine, out_diff};
+  unsigned long long* recs[2] = {rf, rd};
+  for (int l = 0; l < 2; ++l) {
+    const pdd_node_stats& o = *outs[l];
+    const StatPtrs sp{o.mean_phi, o.var_phi, o.mean_cv, o.var_cv, o.cov_phi_xi, o.var_xi, o.rho,
+                      o.se_phi, o.se_cv, o.vr, o.pred_speedup, o.mean_steps,
+                      (unsigned long long*)o.n_paths, (unsigned long long*)o.n_truncated};
+    PDD_CUDA(launch_finalize(recs[l], (uint32_t)n, kappa, sp, c->stream), "finalize launch");
+  }
+  c->launches += 3;
+  if (a->flags & PDD_FLAG_ASYNC) return PDD_OK;
+  WsHeader h{};
+  PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+           "cudaMemcpyAsync(header)");
+  PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (h.err & kErrOverflow) {
+    set_error("pdd_estimate_coupled: a score left the fixed-point range |score| < 32768");
+    return PDD_ERR_OVERFLOW;
+  }
+  if (h.trunc_total > 0) {
+    set_error("pdd_estimate_coupled: %llu paths hit max_steps", h.trunc_total);
+    return PDD_WARN_TRUNCATED;
   }
   return PDD_OK;
 }

@@ -110,6 +110,7 @@ __device__ __forceinline__ void exp_cos_2d(T x, T y, Coef<T>& o, T& u) {
 }
 
 struct Cfg0 {
+  static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 2;
   static constexpr bool kAniso = false;
   static constexpr bool kUnitY = false;
@@ -128,6 +129,7 @@ struct Cfg0 {
 };
 
 struct Aniso {
+  static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 2;
   static constexpr bool kAniso = true;
   static constexpr bool kUnitY = false;
@@ -154,6 +156,7 @@ struct Aniso {
 };
 
 struct Cube3 {
+  static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 3;
   static constexpr bool kAniso = false;
   static constexpr bool kUnitY = false;
@@ -187,7 +190,45 @@ struct Cube3 {
   __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1); }
 };
 
+// The paper's example PDE (Sec. 6): sigma = sqrt(2) I, b = cos(x+y)/(1.1+sin(x+y)) [1,1],
+// c = (x^2+y^2)/(1.1+sin(x+y)), u = 2 cos(2(y-2)x) + sin(3(x-2)y) + 3.1.
+struct PaperEx {
+  static constexpr int kDim = 2;
+  static constexpr bool kAniso = false;
+  static constexpr bool kIsoScaled = true;  // sigma = sa * I with sa = sqrt(2)
+  static constexpr bool kUnitY = false;
+  template <class T, bool GRAD>
+  __device__ __forceinline__ static void eval(T x, T y, T, Coef<T>& o) {
+    T sp, cp, sq, cq, ss, cs;
+    const T p = T(2) * x * (y - T(2)), q = T(3) * y * (x - T(2));
+    m_sincos(p, &sp, &cp);
+    m_sincos(q, &sq, &cq);
+    m_sincos(x + y, &ss, &cs);
+    const T inv = T(1) / (T(1.1) + ss);
+    const T u = T(2) * cp + sq + T(3.1);
+    const T ux = T(-4) * (y - T(2)) * sp + T(3) * y * cq;
+    const T uy = T(-4) * x * sp + T(3) * (x - T(2)) * cq;
+    const T ym2 = y - T(2), xm2 = x - T(2);
+    const T lap = T(-8) * (ym2 * ym2 + x * x) * cp - T(9) * (y * y + xm2 * xm2) * sq;
+    o.b0 = o.b1 = cs * inv;
+    o.b2 = T(0);
+    o.c = (x * x + y * y) * inv;
+    o.f = lap + o.b0 * (ux + uy) - o.c * u;
+    o.g0 = ux;
+    o.g1 = uy;
+    o.g2 = T(0);
+    o.sa = T(1.41421356237309504880);
+  }
+  template <class T>
+  __device__ __forceinline__ static T g(T x, T y, T) {
+    return T(2) * m_cos(T(2) * x * (y - T(2))) + m_sin(T(3) * y * (x - T(2))) + T(3.1);
+  }
+  template <class T>
+  __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1.41421356237309504880); }
+};
+
 struct Harmonic {
+  static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 2;
   static constexpr bool kAniso = false;
   static constexpr bool kUnitY = true;  // c = f = 0: Y = 1, Z = 0 on every path

@@ -98,6 +98,9 @@ cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int
 // Resident blocks per SM of the path kernel of (kind, precision, cv, multi) at
 // `threads` threads per block.
 cudaError_t occupancy_paths(int kind, int precision, int cv, bool multi, int threads, int* occ);
+// Coupled fine (seg[0]) / coarse (seg[1]) pairs, 2D problems, FP32 paths.
+cudaError_t launch_coupled(int kind, int cv, const PathArgs& a, int num_sms, cudaStream_t st,
+                           int* blocks);
 cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, double kappa,
                             const StatPtrs& out, cudaStream_t st);
 // Gradient table of grid values v (FP64, n^D, x fastest) into float2/float4.

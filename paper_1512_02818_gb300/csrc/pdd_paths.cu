@@ -119,7 +119,7 @@ template <class P, class T, int D>
 __device__ __forceinline__ bool should_finish(const PathState<T>& s, T thr0) {
   const T m = (D == 3) ? face_distance(s.x[0], s.x[1], s.x[2]) : face_distance(s.x[0], s.x[1]);
   T thr = thr0;
-  if (P::kAniso) thr *= P::template exit_scale<T>(s.x[0], s.x[1], s.x[2]);
+  if (P::kAniso || P::kIsoScaled) thr *= P::template exit_scale<T>(s.x[0], s.x[1], s.x[2]);
   return m <= thr;
 }
 
@@ -144,6 +144,9 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
   if (P::kAniso) {  // sigma = sqrt(a) [[1, 0], [1/2, sqrt(3)/2]]
     sdW[0] = o.sa * dW0;
     sdW[1] = o.sa * (T(0.5) * dW0 + T(0.86602540378443864676) * dW1);
+  } else if (P::kIsoScaled) {  // sigma = sa I
+    sdW[0] = o.sa * dW0;
+    sdW[1] = o.sa * dW1;
   } else {
     sdW[0] = dW0;
     sdW[1] = dW1;
@@ -183,27 +186,20 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
   s.k += 1;
 }
 
-// Exit scoring: X_tau = Pi(X_k), phi = g(X_tau) Y + Z, xi, and the exact
-// fixed-point accumulation into the node record.
-template <class P, class T, int D, bool MULTI>
-__device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T>& s, bool trunc) {
-  T p[3] = {s.x[0], s.x[1], s.x[2]};
-  project_box<T>(p, D);
-  const T g = P::template g<T>(p[0], p[1], p[2]);
-  const T phi = g * s.Y + (s.Z - s.Zc);
-  const T xi = s.XI - s.XIc;
-  const T psi = phi + xi;
+// Exact fixed-point accumulation of one path's (phi, psi = phi + xi, k) into a
+// node record.
+template <class T>
+__device__ __forceinline__ void accumulate(const PathArgs& a, unsigned long long* w, T phi, T psi,
+                                           int k_steps, bool trunc) {
   long long qa, qb;
   const bool ok = to_fixed(phi, qa) & to_fixed(psi, qb);
   if (!ok) atomicOr(a.err, kErrOverflow);
-  const SegArgs& sg = a.seg[MULTI ? s.seg : 0];
-  unsigned long long* w = sg.acc + (size_t)s.node * kAccWords;
   atomic_add_s64(w + 0, qa);
   atomic_add_prod(w + 2, qa, qa);
   atomic_add_s64(w + 4, qb);
   atomic_add_prod(w + 6, qb, qb);
   atomic_add_prod(w + 8, qa, qb);
-  const unsigned long long k = (unsigned long long)s.k;
+  const unsigned long long k = (unsigned long long)k_steps;
   atomic_add_u128(w + 10, k, 0ull);
   atomic_add_u128(w + 12, k * k, 0ull);
   atomicAdd(w + 14, 1ull);
@@ -211,6 +207,25 @@ __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T
     atomicAdd(w + 15, 1ull);
     atomicAdd(a.trunc_total, 1ull);
   }
+}
+
+// Exit scoring: X_tau = Pi(X_k), phi = g(X_tau) Y + Z, and xi.
+template <class P, class T, int D>
+__device__ __forceinline__ void score_path(const PathState<T>& s, T& phi, T& xi) {
+  T p[3] = {s.x[0], s.x[1], s.x[2]};
+  project_box<T>(p, D);
+  const T g = P::template g<T>(p[0], p[1], p[2]);
+  phi = g * s.Y + (s.Z - s.Zc);
+  xi = s.XI - s.XIc;
+}
+
+// Exit scoring and the exact fixed-point accumulation into the node record.
+template <class P, class T, int D, bool MULTI>
+__device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T>& s, bool trunc) {
+  T phi, xi;
+  score_path<P, T, D>(s, phi, xi);
+  const SegArgs& sg = a.seg[MULTI ? s.seg : 0];
+  accumulate(a, sg.acc + (size_t)s.node * kAccWords, phi, phi + xi, s.k, trunc);
   if (sg.emit_phi != nullptr) {
     const size_t i = (size_t)s.node * sg.emit_stride + s.path;
     sg.emit_phi[i] = (float)phi;
@@ -362,6 +377,151 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
 }
 
 // ---------------------------------------------------------------------------
+// Multilevel coupling (2D): per lane a fine path at h_f = h/2 on the path's
+// own stream and a coarse path at h driven by the sums of pairs of fine
+// increments.  Iteration j uses Philox block j: fine steps 2j and 2j+1 take
+// the pairs (n0, n1) and (n2, n3); coarse step j takes
+// dW = sqrt(h_f) (n0 + n2, n1 + n3), i.e. dW_c = dW_f(2j) + dW_f(2j+1).
+// Each path has its own exit test; when both have finished the lane adds
+// (phi_f, phi_f + xi_f) to the fine records (seg[0].acc) and the differences
+// (phi_f - phi_c, psi_f - psi_c) to the difference records (seg[1].acc).
+// seg[0] holds the fine step and the node / path layout, seg[1] the coarse
+// step; emit pointers of seg[0] / seg[1] receive fine / coarse per-path output.
+// ---------------------------------------------------------------------------
+template <class P, class T, int CV>
+__global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled_2d(
+    const __grid_constant__ PathArgs a) {
+  PathState<T> f, c;
+  LaneSeg<T> lf, lc;
+  init_lane<T, 2>(a, f, lf);
+  init_lane<T, 2>(a, c, lc);
+  load_seg<T, 2>(a.seg[1], lc);
+  bool active = false, exhausted = false;  // active: the pair still has work
+  bool af = false, ac = false;             // fine / coarse path running
+  bool tf = false, tc = false;             // truncated
+  T phif = T(0), xif = T(0), phic = T(0), xic = T(0);
+  uint32_t j = 0;
+  unsigned long long bnext = 0, bend = 0;
+  while (refill<T, 2, false>(a, f, lf, active, bnext, bend, exhausted)) {
+    if (active && f.k == 0 && !af && !ac) {  // refill has just started a new pair in f
+      c = f;
+      af = ac = true;
+      tf = tc = false;
+      j = 0;
+    }
+    if (active) {
+      const uint4 w = path_block<false>(a, 0, j, f.path, f.node);
+      T n[4];
+      box_muller(w.x, w.y, n[0], n[1], lf.sqh);
+      box_muller(w.z, w.w, n[2], n[3], lf.sqh);
+      // fine: two steps
+      if (af) {
+        if (should_finish<P, T, 2>(f, lf.thr0)) {
+          af = false;
+        } else {
+          T d0[3] = {n[0], n[1], T(0)};
+          euler_step<P, T, 2, CV, false>(a, f, lf, d0);
+          if (f.k >= lf.max_steps) {
+            af = false;
+            tf = true;
+          }
+          if (af) {
+            if (should_finish<P, T, 2>(f, lf.thr0)) {
+              af = false;
+            } else {
+              T d1[3] = {n[2], n[3], T(0)};
+              euler_step<P, T, 2, CV, false>(a, f, lf, d1);
+              if (f.k >= lf.max_steps) {
+                af = false;
+                tf = true;
+              }
+            }
+          }
+        }
+        if (!af) score_path<P, T, 2>(f, phif, xif);
+      }
+      // coarse: one step on the summed increments
+      if (ac) {
+        if (should_finish<P, T, 2>(c, lc.thr0)) {
+          ac = false;
+        } else {
+          T dc[3] = {n[0] + n[2], n[1] + n[3], T(0)};
+          euler_step<P, T, 2, CV, false>(a, c, lc, dc);
+          if (c.k >= lc.max_steps) {
+            ac = false;
+            tc = true;
+          }
+        }
+        if (!ac) score_path<P, T, 2>(c, phic, xic);
+      }
+      j += 1;
+      if (!af && !ac) {
+        const SegArgs& s0 = a.seg[0];
+        const SegArgs& s1 = a.seg[1];
+        accumulate(a, s0.acc + (size_t)f.node * kAccWords, phif, phif + xif, f.k, tf);
+        accumulate(a, s1.acc + (size_t)f.node * kAccWords, phif - phic,
+                   (phif + xif) - (phic + xic), c.k, tc);
+        if (s0.emit_phi != nullptr) {
+          const size_t i = (size_t)f.node * s0.emit_stride + f.path;
+          s0.emit_phi[i] = (float)phif;
+          s0.emit_xi[i] = (float)xif;
+          s0.emit_steps[i] = f.k;
+          s1.emit_phi[i] = (float)phic;
+          s1.emit_xi[i] = (float)xic;
+          s1.emit_steps[i] = c.k;
+        }
+        active = false;
+      }
+    }
+  }
+}
+
+template <class P, class T, int CV>
+static cudaError_t launch_coupled_one(const PathArgs& a, int num_sms, cudaStream_t st,
+                                      int* blocks) {
+  const int threads = a.block_threads > 0 ? a.block_threads : kBlockThreads;
+  if (threads % 32 != 0 || threads > kMaxBlockThreads) return cudaErrorInvalidValue;
+  static int occ = 0;
+  if (occ == 0) {
+    int v = 0;
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, paths_coupled_2d<P, T, CV>, threads, 0);
+    if (e != cudaSuccess) return e;
+    occ = v > 0 ? v : 1;
+  }
+  const unsigned long long warps = (a.total + 31ull) / 32ull;
+  const unsigned long long need = (warps + (threads / 32) - 1) / (threads / 32);
+  unsigned long long nb = (unsigned long long)occ * (unsigned long long)num_sms;
+  if (a.max_blocks > 0 && nb > (unsigned long long)a.max_blocks) nb = a.max_blocks;
+  if (nb > need) nb = need;
+  if (nb < 1) nb = 1;
+  *blocks = (int)nb;
+  paths_coupled_2d<P, T, CV><<<(unsigned)nb, (unsigned)threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <class P, class T>
+static cudaError_t launch_coupled_cv(int cv, const PathArgs& a, int sms, cudaStream_t st,
+                                     int* blocks) {
+  switch (cv) {
+    case kCvNone: return launch_coupled_one<P, T, kCvNone>(a, sms, st, blocks);
+    case kCvGrid: return launch_coupled_one<P, T, kCvGrid>(a, sms, st, blocks);
+    default: return launch_coupled_one<P, T, kCvExact>(a, sms, st, blocks);
+  }
+}
+
+cudaError_t launch_coupled(int kind, int cv, const PathArgs& a, int num_sms, cudaStream_t st,
+                           int* blocks) {
+  switch (kind) {
+    case 0: return launch_coupled_cv<Cfg0, float>(cv, a, num_sms, st, blocks);
+    case 1: return launch_coupled_cv<Aniso, float>(cv, a, num_sms, st, blocks);
+    case 3: return launch_coupled_cv<Harmonic, float>(cv, a, num_sms, st, blocks);
+    case 4: return launch_coupled_cv<PaperEx, float>(cv, a, num_sms, st, blocks);
+    default: return cudaErrorInvalidValue;  // 3D coupling is not provided
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Finalisation: one thread per node turns the exact sums into FP64 moments.
 // ---------------------------------------------------------------------------
 __global__ void finalize_nodes(const unsigned long long* __restrict__ acc, uint32_t n_nodes,
@@ -457,6 +617,7 @@ static cudaError_t occupancy_kind(int kind, int cv, int threads, int* occ) {
     case 0: return occupancy_cv<Cfg0, T, MULTI>(cv, threads, occ);
     case 1: return occupancy_cv<Aniso, T, MULTI>(cv, threads, occ);
     case 2: return occupancy_cv<Cube3, T, MULTI>(cv, threads, occ);
+    case 4: return occupancy_cv<PaperEx, T, MULTI>(cv, threads, occ);
     default: return occupancy_cv<Harmonic, T, MULTI>(cv, threads, occ);
   }
 }
@@ -486,6 +647,7 @@ static cudaError_t launch_kind(int kind, int cv, const PathArgs& a, int sms, cud
     case 0: return launch_cv<Cfg0, T, MULTI>(cv, a, sms, st, blocks);
     case 1: return launch_cv<Aniso, T, MULTI>(cv, a, sms, st, blocks);
     case 2: return launch_cv<Cube3, T, MULTI>(cv, a, sms, st, blocks);
+    case 4: return launch_cv<PaperEx, T, MULTI>(cv, a, sms, st, blocks);
     default: return launch_cv<Harmonic, T, MULTI>(cv, a, sms, st, blocks);
   }
 }

@@ -22,6 +22,7 @@ PDD_OK, PDD_ERR_INVALID, PDD_ERR_NOMEM, PDD_ERR_CUDA = 0, -1, -2, -3
 PDD_ERR_TIMEOUT, PDD_ERR_BUSY, PDD_ERR_NOT_READY, PDD_ERR_CANCELLED = -4, -5, -6, -7
 PDD_ERR_OVERFLOW, PDD_WARN_TRUNCATED = -8, 1
 PDD_PROBLEM_CFG0_2D, PDD_PROBLEM_ANISO_2D, PDD_PROBLEM_CUBE_3D, PDD_PROBLEM_HARMONIC_2D = 0, 1, 2, 3
+PDD_PROBLEM_PAPER_EX_2D = 4
 PDD_EXIT_GOBET_MENOZZI, PDD_EXIT_NAIVE = 0, 1
 PDD_Y_EULER, PDD_Y_EXP = 0, 1
 PDD_PATH_FP32, PDD_PATH_FP64 = 0, 1
@@ -145,6 +146,8 @@ _SIGS = [
                                          ctypes.POINTER(FitOut)]),
     ("pdd_schedule", ctypes.c_int, [ctypes.POINTER(ScheduleArgs), ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("pdd_estimate_coupled", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
+                                            ctypes.POINTER(NodeStats), ctypes.POINTER(NodeStats)]),
     ("pdd_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerDesc),
                                          ctypes.POINTER(ctypes.c_void_p)]),
     ("pdd_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
@@ -310,6 +313,12 @@ def pdd_schedule(K, beta, alpha, V_phi, V_psi, rho, delta: float, kappa: float, 
     J = n.value
     n_sp = J + 1 if J < max_levels else J
     return a[: J + 1].copy(), sp[:n_sp].copy()
+
+
+def pdd_estimate_coupled(problem: int, args: EstimateArgs, out_fine: NodeStats,
+                         out_diff: NodeStats) -> int:
+    return _check(lib().pdd_estimate_coupled(problem, ctypes.byref(args), ctypes.byref(out_fine),
+                                             ctypes.byref(out_diff)))
 
 
 def pdd_server_create(ctx: int, desc: ServerDesc | None = None) -> int:
@@ -551,6 +560,29 @@ class Problem:
         st = pdd_estimate_levels(self.handle, [p[0] for p in prepared], [p[1] for p in prepared],
                                  flags)
         return st, [p[2] for p in prepared]
+
+    def estimate_coupled(self, nodes, n_paths: int, dt: float, grid_id: int = PDD_CV_NONE,
+                         seed: int = 1234, stream_tag: int = 0, emit_paths: bool = False):
+        """Multilevel coupling (fine dt/2, coarse dt).  Returns (fine, diff)
+        dicts of per-node CUDA tensors; with emit_paths, fine['phi'] etc. hold
+        the fine paths and diff['phi'] etc. the coarse paths."""
+        torch = _torch()
+        args, out_f, res_f = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, 1.0,
+                                           False, True, False, False)
+        _, out_d, res_d = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, 1.0,
+                                        False, True, False, False)
+        if emit_paths:
+            n = args.n_nodes
+            dev = torch.device("cuda", self.ctx.device)
+            phi = torch.empty((2, n, n_paths), dtype=torch.float32, device=dev)
+            xi = torch.empty((2, n, n_paths), dtype=torch.float32, device=dev)
+            st = torch.empty((2, n, n_paths), dtype=torch.int32, device=dev)
+            args.flags |= PDD_FLAG_EMIT_PATHS
+            args.path_phi, args.path_xi, args.path_steps = phi.data_ptr(), xi.data_ptr(), st.data_ptr()
+            res_f.update(phi=phi[0], xi=xi[0], steps=st[0])
+            res_d.update(phi=phi[1], xi=xi[1], steps=st[1])
+        res_f["status"] = pdd_estimate_coupled(self.handle, args, out_f, out_d)
+        return res_f, res_d
 
     def accumulate(self, nodes, n_paths: int, dt: float, records, path_offset: int = 0,
                    grid_id: int = PDD_CV_NONE, seed: int = 1234, stream_tag: int = 0):

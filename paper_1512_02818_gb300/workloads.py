@@ -16,6 +16,9 @@ Workloads (all on the unit box, the boxes split into equal subdomains):
   1e-3 on a 65^3 grid, v = u + eps sin(3 pi x) sin(2 pi y) sin(pi z)).
 * ``c4`` -- 2D anisotropic diffusion, 32x32 subdomains, 1,984 segments x 16 =
   31,744 nodes, 10^4 paths, dt = 1e-4, eps = 1e-2 on 513^2.
+* ``paper`` -- the paper's example PDE on an assumed domain (its Fig. 1 is
+  missing): the unit box cut into 4 vertical strips, 3 interfaces x 6 nodes =
+  18 nodes.
 
 Node placement on an interface segment of length L: n equispaced interior
 points j L / (n+1), j = 1..n (end points excluded).  Canonical node order
@@ -29,7 +32,7 @@ import math
 
 import numpy as np
 
-CFG0_2D, ANISO_2D, CUBE_3D, HARMONIC_2D = 0, 1, 2, 3
+CFG0_2D, ANISO_2D, CUBE_3D, HARMONIC_2D, PAPER_EX_2D = 0, 1, 2, 3, 4
 
 
 def nodes_2d(subdomains: int, per_segment: int) -> np.ndarray:
@@ -44,6 +47,14 @@ def nodes_2d(subdomains: int, per_segment: int) -> np.ndarray:
                     a = i * L
                     t = s * L + j * L / (n + 1)
                     pts.append((a, t) if axis == 0 else (t, a))
+    return np.asarray(pts, dtype=np.float32).reshape(-1, 2)
+
+
+def nodes_strips(strips: int, per_interface: int) -> np.ndarray:
+    """(n, 2) float32 nodes of [0,1]^2 cut into vertical strips: interfaces
+    x = i/strips (i = 1..strips-1), per_interface interior points each."""
+    pts = [(i / strips, j / (per_interface + 1)) for i in range(1, strips)
+           for j in range(1, per_interface + 1)]
     return np.asarray(pts, dtype=np.float32).reshape(-1, 2)
 
 
@@ -77,6 +88,9 @@ def exact_u(kind: int, x: np.ndarray) -> np.ndarray:
                 + x[..., 0] * x[..., 1] * x[..., 2])
     if kind == HARMONIC_2D:
         return x[..., 0] ** 2 - x[..., 1] ** 2
+    if kind == PAPER_EX_2D:
+        X, Y = x[..., 0], x[..., 1]
+        return 2 * np.cos(2 * (Y - 2) * X) + np.sin(3 * (X - 2) * Y) + 3.1
     raise ValueError(kind)
 
 
@@ -113,6 +127,8 @@ WORKLOADS = {
 
 
 def workload_nodes(name: str) -> np.ndarray:
+    if name == "paper":
+        return nodes_strips(4, 6)
     w = WORKLOADS[name]
     if w["dim"] == 3:
         return nodes_3d(w["subdomains"], w["per_segment"])

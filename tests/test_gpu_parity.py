@@ -49,6 +49,9 @@ CASES = [
     ("cube_exact_cv", 2, ("c2", 1531, 6), 250, 1e-3, "exact", None, "gm", False),
     ("harmonic_naive", 3, ("c0", 3, 8), 1000, 1e-3, "none", None, "naive", False),
     ("c0_yexp_exact", 0, ("c0", 3, 8), 500, 1e-3, "exact", None, "gm", True),
+    ("paper_plain", 4, ("paper", 1, 18), 500, 1e-3, "none", None, "gm", False),
+    ("paper_grid_cv", 4, ("paper", 1, 18), 400, 5e-4, "grid", (65, 1e-2), "gm", False),
+    ("paper_exact_naive", 4, ("paper", 2, 9), 400, 1e-3, "exact", None, "naive", False),
 ]
 
 

@@ -34,6 +34,13 @@ def _sym_problem(kind):
         c = sympy.Integer(1)
         A = sympy.eye(3)
         X = [x, y, z]
+    elif kind == 4:  # the paper's example, eq. F:PDE_ejemplo (sigma = sqrt(2) I)
+        u = 2 * sympy.cos(2 * (y - 2) * x) + sympy.sin(3 * (x - 2) * y) + sympy.Rational(31, 10)
+        den = sympy.Rational(11, 10) + sympy.sin(x + y)
+        b = [sympy.cos(x + y) / den, sympy.cos(x + y) / den]
+        c = (x**2 + y**2) / den
+        A = 2 * sympy.eye(2)
+        X = [x, y]
     else:
         u = x**2 - y**2
         b = [0, 0]
@@ -48,7 +55,7 @@ def _sym_problem(kind):
     return X, u, f, grad, A, b, c
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3, 4])
 def test_coefficients_solve_the_pde(oracle_mod, kind):
     X, u, f, grad, A, b, c = _sym_problem(kind)
     D = len(X)

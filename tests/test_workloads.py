@@ -5,7 +5,8 @@ import pytest
 from paper_1512_02818_gb300 import workloads as W
 
 
-@pytest.mark.parametrize("name,count", [("c0", 24), ("c1", 256), ("c2", 9216), ("c4", 31744)])
+@pytest.mark.parametrize("name,count", [("c0", 24), ("c1", 256), ("c2", 9216), ("c4", 31744),
+                                        ("paper", 18)])
 def test_node_counts(name, count):
     nodes = W.workload_nodes(name)
     assert nodes.shape[0] == count and nodes.dtype == np.float32
