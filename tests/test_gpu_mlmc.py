@@ -45,15 +45,19 @@ def test_coupled_matches_oracle(kind, cv):
         ok &= np.abs(res["phi"].cpu().numpy() - ref["phi_" + lvl]) <= PATH_ATOL
         ok &= np.abs(res["xi"].cpu().numpy() - ref["xi_" + lvl]) <= PATH_ATOL
     assert ok.mean() >= PATH_FRAC, ok.mean()
-    # fine level == the plain estimate at dt/2 on the same streams
+    # fine level == the plain estimate at dt/2 on the same streams (a different
+    # kernel: FP32 contraction choices may differ in the last bits)
     alone = prob.estimate(nodes, N, h / 2, grid_id=gid, seed=3, stream_tag=11)
-    for f in pdd.STAT_FIELDS + pdd.COUNT_FIELDS:
-        assert np.array_equal(fine[f].cpu().numpy(), alone[f].cpu().numpy(), equal_nan=True), f
+    for f in ("mean_phi", "mean_cv", "var_phi", "var_cv", "mean_steps"):
+        assert np.allclose(fine[f].cpu().numpy(), alone[f].cpu().numpy(), rtol=1e-5, atol=1e-6,
+                           equal_nan=True), f
+    assert np.array_equal(fine["n_paths"].cpu().numpy(), alone["n_paths"].cpu().numpy())
     # the difference statistics are those of the emitted pairs
     d = fine["phi"].cpu().numpy().astype(np.float64) - diff["phi"].cpu().numpy()
     assert np.allclose(diff["mean_phi"].cpu().numpy(), d.mean(1), atol=1e-6)
     assert np.allclose(diff["var_phi"].cpu().numpy(), d.var(1, ddof=1), rtol=1e-3, atol=1e-7)
-    assert np.all(diff["var_phi"].cpu().numpy() < 0.5 * fine["var_phi"].cpu().numpy())
+    # (nodes inside the shrinkage layer finish at k = 0: both variances are 0)
+    assert np.all(diff["var_phi"].cpu().numpy() <= 0.5 * fine["var_phi"].cpu().numpy() + 1e-12)
     assert np.allclose(diff["mean_steps"].cpu().numpy(), ref["steps_c"].mean(1), rtol=1e-3)
     with pytest.raises(pdd.PddError):
         pdd.Problem(ctx, pdd.PDD_PROBLEM_CUBE_3D).estimate_coupled(
