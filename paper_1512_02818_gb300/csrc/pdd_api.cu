@@ -356,6 +356,7 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
     sg.begin = begin;
     sg.total = (unsigned long long)a.n_nodes * (unsigned long long)a.n_paths;
     sg.n_paths = (unsigned long long)a.n_paths;
+    sg.n_nodes = (unsigned long long)a.n_nodes;
     sg.acc = acc + (size_t)rec_base[l] * kAccWords;
     sg.path_off = 0;
     sg.emit_stride = (unsigned long long)a.n_paths;
@@ -869,6 +870,7 @@ int pdd_accumulate(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_off
   sg.begin = 0;
   sg.total = (unsigned long long)a->n_nodes * (unsigned long long)a->n_paths;
   sg.n_paths = (unsigned long long)a->n_paths;
+  sg.n_nodes = (unsigned long long)a->n_nodes;
   sg.acc = (unsigned long long*)records;
   sg.grad = lp.table;
   sg.emit_stride = 0;
@@ -1023,6 +1025,7 @@ int pdd_estimate_coupled(pdd_problem* p, const pdd_estimate_args* a, pdd_node_st
     sg.begin = 0;
     sg.total = pa.total;
     sg.n_paths = (unsigned long long)a->n_paths;
+    sg.n_nodes = (unsigned long long)n;
     sg.acc = l == 0 ? rf : rd;
     sg.grad = lp.table;
     const size_t off = l == 0 ? 0 : n * (size_t)a->n_paths;

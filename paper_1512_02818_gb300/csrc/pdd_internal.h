@@ -29,6 +29,7 @@ struct SegArgs {
   unsigned long long begin;    // first index of the segment in the launch's flat path space
   unsigned long long total;    // n_nodes * n_paths
   unsigned long long n_paths;  // paths per node in this segment
+  unsigned long long n_nodes;  // nodes of this segment
   unsigned long long* acc;     // node records of the segment's nodes (16 words each)
   const void* grad;            // float2 (2D) / float4 (3D) gradient table; null: no grid
   float* emit_phi;             // optional per-path outputs: [node * emit_stride + path]

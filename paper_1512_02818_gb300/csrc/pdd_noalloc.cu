@@ -167,6 +167,7 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   sg.begin = 0;
   sg.total = pa.total;
   sg.n_paths = (unsigned long long)a->n_paths;
+  sg.n_nodes = (unsigned long long)n;
   sg.acc = acc;
   sg.path_off = 0;
   sg.emit_stride = (unsigned long long)a->n_paths;

@@ -4,11 +4,14 @@
 // .. F:Rho, F:Pointwise_cost, F:VR_Pointwise_cost, F:nu).
 //
 // Execution model.  One path per lane.  The paths of all nodes form one flat
-// index space g = node * n_paths + path; warps take batches of 32 indices
-// from a global cursor (atomicAdd) and every lane whose path has finished
-// takes the next index of its warp's batch at the next iteration boundary, so
-// lanes stay busy whatever the spread of exit times (paths of one node range
-// over ~12x the mean number of steps).  The grid is persistent (occupancy x
+// path-major index space g = path * n_nodes + node (consecutive indices are
+// different nodes, so the paths in flight at any moment spread their record
+// atomics over all node records instead of queueing on one record's cache
+// line); warps take batches of 32 indices from a global cursor (atomicAdd)
+// and every lane whose path has finished takes the next index of its warp's
+// batch at the next iteration boundary, so lanes stay busy whatever the
+// spread of exit times (paths of one node range over ~12x the mean number of
+// steps).  The grid is persistent (occupancy x
 // SM count blocks).  Per-node sums are exact integers, so which lane or warp
 // runs a path changes nothing in the results.
 //
@@ -97,12 +100,14 @@ __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long
   const SegArgs& sg = a.seg[si];
   const unsigned long long li = g - sg.begin;
   if (sg.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
-    const uint32_t gg = (uint32_t)li, np = (uint32_t)sg.n_paths;
-    s.node = gg / np;
-    s.path = sg.path_off + (gg - s.node * np);
+    const uint32_t gg = (uint32_t)li, nn = (uint32_t)sg.n_nodes;
+    const uint32_t p = gg / nn;
+    s.node = gg - p * nn;
+    s.path = sg.path_off + p;
   } else {
-    s.node = (uint32_t)(li / sg.n_paths);
-    s.path = sg.path_off + (uint32_t)(li - (unsigned long long)s.node * sg.n_paths);
+    const unsigned long long p = li / sg.n_nodes;
+    s.node = (uint32_t)(li - p * sg.n_nodes);
+    s.path = sg.path_off + (uint32_t)p;
   }
   s.seg = si;
   s.x[0] = (T)__ldg(sg.cx + s.node);

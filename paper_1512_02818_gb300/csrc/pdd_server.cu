@@ -292,6 +292,7 @@ bool issue_launch(pdd_server* s) {
     sg.begin = begin;
     sg.total = (unsigned long long)r->n_nodes * m;
     sg.n_paths = m;
+    sg.n_nodes = (unsigned long long)r->n_nodes;
     sg.acc = req_acc(s, *r);
     sg.grad = r->table;
     sg.emit_phi = nullptr;
