@@ -583,7 +583,10 @@ def run_c3(args):
                 "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat else None,
                 "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat else None,
                 "completed_path_steps_per_s": done_steps / elapsed,
-                "completed_nodes_per_s": done_nodes / elapsed, "elapsed_s": elapsed}
+                "completed_nodes_per_s": done_nodes / elapsed, "elapsed_s": elapsed,
+                # every path-step the retired launches ran, including the slices of
+                # requests still running (or cancelled) when the window closed
+                "executed_path_steps_per_s": stats["path_steps"] / elapsed}
 
     clocks = ClockSampler(smi_id(0))
     # capacity: one large request (256 nodes x 1e5 paths, dt 1e-4, eps 1e-2) alone

@@ -365,6 +365,8 @@ typedef struct {
 typedef struct {
   int64_t submitted, admitted, rejected_busy, rejected_invalid, rejected_nomem;
   int64_t completed, cancelled, failed, launches, pending, active;
+  int64_t path_steps;  /* Euler steps executed by retired launches, whether or not
+                          their requests later completed */
 } pdd_server_stats;
 
 int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** out);

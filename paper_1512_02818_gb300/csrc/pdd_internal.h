@@ -51,6 +51,7 @@ struct PathArgs {
   unsigned long long* cursor;  // flat path cursor, zeroed before the launch
   unsigned* err;               // error bits (kErr*)
   unsigned long long* trunc_total;
+  unsigned long long* steps_total;  // optional: sum of the exit indices of all paths run
   int y_exp;
   int max_blocks;              // 0 = occupancy x SM count
   int block_threads;           // 0 = default (256)

@@ -212,6 +212,7 @@ __device__ __forceinline__ void accumulate(const PathArgs& a, unsigned long long
     atomicAdd(w + 15, 1ull);
     atomicAdd(a.trunc_total, 1ull);
   }
+  if (a.steps_total != nullptr) atomicAdd(a.steps_total, k);
 }
 
 // Exit scoring: X_tau = Pi(X_k), phi = g(X_tau) Y + Z, and xi.

@@ -119,6 +119,7 @@ struct Request {
 
 struct Launch {
   cudaEvent_t ev = nullptr;
+  int stream = 0;
   std::vector<uint64_t> tickets;
 };
 
@@ -133,7 +134,8 @@ struct pdd_server {
   int next_stream = 0;
   char* dev_arena = nullptr;
   char* host_arena = nullptr;  // page-locked results
-  char* hdr = nullptr;         // per-launch header slots (cursor, err, trunc): 2 x 256 B
+  char* hdr = nullptr;         // per-launch header slots (cursor, err, trunc, steps): 2 x 256 B
+  unsigned long long* steps_host = nullptr;  // page-locked: path-steps of the last launch per stream
   Arena dmem, hmem;
   std::mutex mu;
   std::condition_variable cv_done, cv_work;
@@ -271,6 +273,7 @@ bool issue_launch(pdd_server* s) {
   pa.cursor = (unsigned long long*)hdr;
   pa.err = (unsigned*)(hdr + 8);
   pa.trunc_total = (unsigned long long*)(hdr + 16);
+  pa.steps_total = (unsigned long long*)(hdr + 24);
   pa.y_exp = pv.y_rule == PDD_Y_EXP;
   int bt = 0, mb = 0, dev = 0, sms = 0;
   ctx_view(s->ctx, &dev, &sms, &bt, &mb);
@@ -318,6 +321,12 @@ bool issue_launch(pdd_server* s) {
   pa.total = begin;
   int blocks = 0;
   if (e == cudaSuccess) e = launch_paths(pv.kind, pv.precision, cv, pa, s->num_sms, st, &blocks);
+  // the launch's executed path-steps, read when its event has completed; the
+  // slot is not reused before then (the next launch on this stream is issued
+  // after this one retires)
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->steps_host + sidx, pa.steps_total, 8, cudaMemcpyDeviceToHost, st);
+  L.stream = sidx;
   s->st.launches++;
   // requests whose last slice is in this launch: finalise and copy out
   const cudaEvent_t prev = s->inflight.empty() ? nullptr : s->inflight.back().ev;
@@ -365,6 +374,7 @@ bool issue_launch(pdd_server* s) {
 void retire(pdd_server* s) {
   while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().ev) == cudaSuccess) {
     Launch& L = s->inflight.front();
+    s->st.path_steps += (int64_t)s->steps_host[L.stream];
     for (uint64_t t : L.tickets) {
       auto it = s->reqs.find(t);
       if (it != s->reqs.end()) it->second->inflight -= 1;
@@ -452,6 +462,7 @@ int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** ou
   cudaError_t e = cudaMalloc((void**)&s->dev_arena, d.device_arena_bytes);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_arena, host_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->hdr, 512);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->steps_host, 2 * sizeof(unsigned long long));
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     e = cudaStreamCreateWithFlags(&s->stream[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
@@ -460,6 +471,7 @@ int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** ou
     if (s->dev_arena) cudaFree(s->dev_arena);
     if (s->host_arena) cudaFreeHost(s->host_arena);
     if (s->hdr) cudaFree(s->hdr);
+    if (s->steps_host) cudaFreeHost(s->steps_host);
     for (auto& x : s->stream)
       if (x) cudaStreamDestroy(x);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
@@ -700,6 +712,7 @@ void pdd_server_destroy(pdd_server* s) {
   cudaFree(s->dev_arena);
   cudaFreeHost(s->host_arena);
   cudaFree(s->hdr);
+  cudaFreeHost(s->steps_host);
   for (auto& x : s->stream) cudaStreamDestroy(x);
   cudaStreamDestroy(s->copy_stream);
   delete s;

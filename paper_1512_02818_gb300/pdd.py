@@ -99,7 +99,7 @@ class ServerDesc(ctypes.Structure):
 
 SERVER_STAT_FIELDS = ["submitted", "admitted", "rejected_busy", "rejected_invalid",
                       "rejected_nomem", "completed", "cancelled", "failed", "launches", "pending",
-                      "active"]
+                      "active", "path_steps"]
 
 
 class ServerStats(ctypes.Structure):

@@ -73,6 +73,9 @@ def test_mix_equals_alone(env):
     s = srv.stats()
     assert s["completed"] == len(reqs) and s["admitted"] == len(reqs)
     assert s["launches"] > len(reqs) // 8  # requests were spread over several launches
+    # the launches' executed path-steps are exactly the requests' exit indices
+    steps = sum(int(np.rint(_alone(prob, r)["mean_steps"] * r["n_paths"]).sum()) for r in reqs)
+    assert s["path_steps"] == steps
     srv.close()
 
 
