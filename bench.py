@@ -69,11 +69,13 @@ def parse_args():
                     help="keep the library's default launch shape")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 64 of the 256 nodes x 2e4 paths (same kernels)")
-    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit"], default="c1",
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit", "mlmc"],
+                    default="c1",
                     help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c0: 24 nodes, "
                          "plain, dt 1e-3; fit: Algorithm 3 on the 24 nodes; c2: 3D "
                          "three-level cascade in one launch (CUDA graph); c3: serving with "
-                         "Poisson arrivals; c4: anisotropic 2D, FP32 vs FP64 paths")
+                         "Poisson arrivals; c4: anisotropic 2D, FP32 vs FP64 paths; mlmc: "
+                         "multilevel driver at a fixed RMSE vs the single level")
     ap.add_argument("--window", type=float, default=10.0, help="c3: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="c3: arrivals per second")
     return ap.parse_args()
@@ -792,13 +794,81 @@ def run_fit(args):
     return out
 
 
+def run_mlmc(args):
+    """Multilevel Monte Carlo (pdd_mlmc) on the 256-node 2D workload at a fixed
+    RMSE, plain and with the eps = 1e-2 control grid, against the single-level
+    estimator at the multilevel run's finest step with the same node-mean
+    variance budget (N = ceil(2 Vbar / a^2) from a pilot run)."""
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    ctx = pdd.Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    prob.set_control_grid(0, W.control_grid(0, GRID_N, 1e-2))
+    nodes = W.workload_nodes("c1")
+    dev = torch.device("cuda", 0)
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).to(dev) for j in range(2)]
+    u = W.exact_u(0, nodes.astype(np.float64))
+    a_t, dt0 = 1e-3, 1.6e-2
+    clocks = ClockSampler(smi_id(0))
+    modes = {}
+    for name, gid in (("plain", pdd.PDD_CV_NONE), ("cv_eps1e-2", 0)):
+        kw = dict(grid_id=gid, min_levels=2, max_levels=8, n_pilot=2000, stream_tag_base=300)
+        prob.mlmc(nodes, dt0, a_t, **kw)  # warm-up (same work)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = prob.mlmc(nodes, dt0, a_t, **kw)
+        secs = time.perf_counter() - t0
+        hL = dt0 / 2 ** (r["n_levels"] - 1)
+        # single level at h_L: pilot variance, then N for the same variance budget
+        pilot = prob.estimate(cols, 20000, hL, grid_id=gid, stream_tag=500)
+        vcol = "var_phi" if gid == pdd.PDD_CV_NONE else "var_cv"
+        n_sl = int(np.ceil(2.0 * float(pilot[vcol].mean().item()) / a_t**2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sl = prob.estimate(cols, n_sl, hL, grid_id=gid, stream_tag=501)
+        torch.cuda.synchronize()
+        secs_sl = time.perf_counter() - t0
+        mcol = "mean_phi" if gid == pdd.PDD_CV_NONE else "mean_cv"
+        m_sl = sl[mcol].cpu().numpy()
+        sl_steps = float((sl["mean_steps"].cpu().numpy() * n_sl).sum())
+        modes[name] = {
+            "status": int(r["status"]), "levels": int(r["n_levels"]), "rounds": int(r["rounds"]),
+            "finest_dt": hL, "n_paths": [int(x) for x in r["n_paths"]],
+            "var_mean": [float(x) for x in r["var_mean"]],
+            "cost_mean": [float(x) for x in r["cost_mean"]],
+            "bias_estimate": float(r["bias_estimate"]), "seconds": secs,
+            "path_steps": int(r["path_steps"]), "nodes_per_s": len(nodes) / secs,
+            "rmse_vs_exact": float(np.sqrt(np.mean((r["estimate"] - u) ** 2))),
+            "extrapolated_rmse_vs_exact": float(np.sqrt(np.mean((r["extrapolated"] - u) ** 2))),
+            "single_level": {"n_paths": n_sl, "seconds": secs_sl, "path_steps": sl_steps,
+                             "nodes_per_s": len(nodes) / secs_sl,
+                             "rmse_vs_exact": float(np.sqrt(np.mean((m_sl - u) ** 2)))},
+            "speedup_vs_single_level": secs_sl / secs,
+        }
+    clk = clocks.stop()
+    prob.close()
+    ctx.close()
+    return {"workload": "mlmc", "metric": METRIC, "value": modes["cv_eps1e-2"]["nodes_per_s"],
+            "unit": "nodes/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "multilevel Monte Carlo on the 2D CFG0 problem, 256 nodes, "
+                                   "target RMSE 1e-3, dt0 = 1.6e-2 halved per level (2-8 levels), "
+                                   "2000 pilot paths, Gobet-Menozzi, alpha = 1; plain and "
+                                   "eps = 1e-2 control grid 129^2"},
+            "modes": modes, "clocks": clk}
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_info()
     if args.workload != "c1" and args.impl == "ours":
         if rank == 0:
             fn = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "c4": run_c4,
-                  "fit": run_fit}[args.workload]
+                  "fit": run_fit, "mlmc": run_mlmc}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":

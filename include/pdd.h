@@ -65,7 +65,8 @@ typedef enum {
   PDD_ERR_NOT_READY = -6, /* poll: request still running */
   PDD_ERR_CANCELLED = -7, /* poll: request was cancelled */
   PDD_ERR_OVERFLOW = -8,  /* a score left the fixed-point range |score| < 32768 */
-  PDD_WARN_TRUNCATED = 1  /* results valid, but some paths hit max_steps */
+  PDD_WARN_TRUNCATED = 1, /* results valid, but some paths hit max_steps */
+  PDD_WARN_NOT_CONVERGED = 2 /* pdd_mlmc: results valid, stopping test not met */
 } pdd_status;
 
 /* Built-in problems on the unit box [0,1]^D (the synthetic workloads).     */
@@ -259,10 +260,10 @@ int pdd_finalize_records(pdd_ctx* ctx, const uint64_t* records, int64_t n_nodes,
 int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes);
 
 /* Multilevel coupling (the multilevel Monte Carlo variant the paper names as
-   future work, Sec. 1 and Sec. 7), 2D problems with FP32 paths.  For every
-   (node, path) the library runs a FINE path at h/2 = args->dt / 2 on the
-   path's own random stream (the same path pdd_estimate_nodes runs at dt/2)
-   and a COARSE path at h = args->dt driven by the sums of pairs of fine
+   future work, Sec. 1 and Sec. 7), 2D and 3D problems with FP32 paths.  For
+   every (node, path) the library runs a FINE path at h/2 = args->dt / 2 on
+   the path's own random stream (the same path pdd_estimate_nodes runs at
+   dt/2) and a COARSE path at h = args->dt driven by the sums of pairs of fine
    increments, dW_c(k) = dW_f(2k) + dW_f(2k+1); each path has its own exit.
    out_fine receives the statistics of the fine level (as pdd_estimate_nodes
    at dt/2); out_diff those of the level difference: mean_phi / var_phi of
@@ -270,9 +271,77 @@ int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes);
    mean_steps of the coarse path.  The difference has a small variance, so
    E[phi_h/2] - E[phi_h] is cheap to resolve (the multilevel telescoping sum).
    Coordinates and outputs are device pointers; with PDD_FLAG_EMIT_PATHS the
-   per-path arrays hold 2 x n_nodes x n_paths entries, fine first.          */
+   per-path arrays hold 2 x n_nodes x n_paths entries, fine first.
+   pdd_accumulate_coupled runs pairs path_offset .. path_offset + n_paths - 1
+   and adds their exact sums into rec_fine / rec_diff (device, n_nodes x
+   PDD_RECORD_WORDS each, zeroed by the caller before the first call), the
+   records pdd_finalize_records turns into the two statistics above.        */
 int pdd_estimate_coupled(pdd_problem* problem, const pdd_estimate_args* args,
                          pdd_node_stats* out_fine, pdd_node_stats* out_diff);
+int pdd_accumulate_coupled(pdd_problem* problem, const pdd_estimate_args* args,
+                           uint64_t path_offset, uint64_t* rec_fine, uint64_t* rec_diff);
+
+/* Multilevel Monte Carlo estimate of the nodal values (the MLMC variant the
+   paper leaves to future work, Sec. 1 and Sec. 7; the level-adaptive
+   sample allocation is Giles' standard one).  Level 0 is Algorithm 1 at
+   h_0 = dt0; level l >= 1 is the coupled difference phi_{h_l} - phi_{h_(l-1)},
+   h_l = dt0 / 2^l (pdd_accumulate_coupled with dt = h_(l-1)); level l draws
+   stream_tag_base + l.  With a control grid (or PDD_CV_EXACT) every level
+   uses the controlled score phi + xi.  Starting from min_levels levels with
+   n_pilot paths each, the driver repeats:
+     1. run the missing paths of every level (path indices continue, so the
+        result equals one run with the final counts);
+     2. from the records: per node the level mean m_l,i and variance v_l,i,
+        and the cost c_l,i (mean exit index, fine + coarse for l >= 1);
+        Vbar_l, Cbar_l = their node means;
+     3. N_l = ceil(2 eps^-2 sqrt(Vbar_l / Cbar_l) sum_k sqrt(Vbar_k Cbar_k))
+        (pdd_mlmc_allocate: least total cost with node-mean variance
+        sum_l Vbar_l / N_l <= eps^2 / 2);
+     4. when every level has its N_l: the bias estimate
+        b = max(r_L, r_(L-1) / 2^alpha) / (2^alpha - 1), where r_l is the
+        node-RMS of m_l,i with the sampling noise v_l,i / N_l removed; stop
+        if b <= eps / sqrt(2), else add a level (up to max_levels).
+   Per node: estimate = sum_l m_l,i, variance = sum_l v_l,i / N_l, and the
+   Talay-Tubaro (Richardson) extrapolation on the finest pair,
+   extrapolated = estimate + m_L,i / (2^alpha - 1), with its variance
+   sum_(l<L) v_l,i / N_l + (2^alpha / (2^alpha - 1))^2 v_L,i / N_L.
+   Output arrays are host arrays of n_nodes (any may be NULL).  Returns
+   PDD_OK when converged, PDD_WARN_NOT_CONVERGED when max_levels, the round
+   cap (64) or the 2^32 path limit stopped it first (outputs valid), or an
+   error status.                                                            */
+#define PDD_MLMC_MAX_LEVELS 16
+typedef struct {
+  int64_t n_nodes;
+  const float* coords[3];     /* device SoA coordinates */
+  int32_t grid_id;            /* control grid, PDD_CV_NONE or PDD_CV_EXACT */
+  int32_t min_levels;         /* 2 .. max_levels */
+  int32_t max_levels;         /* min_levels .. PDD_MLMC_MAX_LEVELS */
+  int32_t reserved;
+  double dt0;                 /* step of level 0 */
+  int64_t n_pilot;            /* first paths of every level, >= 2 */
+  double target_rmse;         /* eps > 0: node-mean MSE against u <= eps^2 */
+  double alpha;               /* weak order (1 with the Gobet-Menozzi test) */
+  uint64_t seed;
+  uint32_t stream_tag_base;
+  uint32_t reserved2;
+} pdd_mlmc_args;
+typedef struct {
+  double* estimate;           /* n_nodes (host, nullable) */
+  double* variance;           /* n_nodes */
+  double* extrapolated;       /* n_nodes: Talay-Tubaro on the finest pair */
+  double* extrap_variance;    /* n_nodes */
+  int32_t n_levels;           /* levels used, L + 1 */
+  int32_t rounds;             /* passes of steps 1-4 */
+  int64_t n_paths[PDD_MLMC_MAX_LEVELS];   /* N_l */
+  double var_mean[PDD_MLMC_MAX_LEVELS];   /* Vbar_l */
+  double cost_mean[PDD_MLMC_MAX_LEVELS];  /* Cbar_l, path-steps per sample */
+  double corr_rms[PDD_MLMC_MAX_LEVELS];   /* r_l */
+  double bias_estimate;       /* b of the last test */
+  int64_t path_steps;         /* path-steps of all levels (exit indices summed) */
+} pdd_mlmc_out;
+int pdd_mlmc_allocate(int n_levels, const double* var_mean, const double* cost_mean,
+                      double target_rmse, int64_t* n_paths);
+int pdd_mlmc(pdd_problem* problem, const pdd_mlmc_args* args, pdd_mlmc_out* out);
 
 /* Fast fit of nodal constants (Algorithm 3, Sec. 5 H5).  For every node the
    library runs n_paths realisations of Algorithm 1 at each of n_h equispaced

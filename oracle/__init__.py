@@ -84,8 +84,8 @@ def _load():
         lib.or_sample_paths.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, P, P, P,
                                         dbl, u64, u32, P, P, P]
         lib.or_sample_paths.restype = i32
-        lib.or_coupled_paths.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, i64, dbl, u64,
-                                         u32, P, P, P, P, P, P]
+        lib.or_coupled_paths.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, P, i64, dbl,
+                                         u64, u32, P, P, P, P, P, P]
         lib.or_coupled_paths.restype = i32
         assert lib.or_nstat() == len(STAT_NAMES)
         _lib = lib
@@ -395,10 +395,12 @@ def coupled_paths(kind, nodes, n_paths, h, seed=1234, tag=0, cv=CV_NONE, grad=No
     stream) and the coarse path at h driven by the sums of pairs of fine
     increments.  Returns per-path arrays (n_nodes, n_paths)."""
     lib = _load()
-    nodes = np.asarray(nodes, dtype=np.float64).reshape(-1, 2)
+    dim = 3 if kind == CUBE_3D else 2
+    nodes = np.asarray(nodes, dtype=np.float64).reshape(-1, dim)
     n = nodes.shape[0]
     xs = np.ascontiguousarray(nodes[:, 0])
     ys = np.ascontiguousarray(nodes[:, 1])
+    zs = np.ascontiguousarray(nodes[:, 2]) if dim == 3 else None
     if max_steps is None:
         max_steps = default_max_steps(0.5 * h)
     tot = n * n_paths
@@ -408,9 +410,69 @@ def coupled_paths(kind, nodes, n_paths, h, seed=1234, tag=0, cv=CV_NONE, grad=No
     if grad is not None:
         grad = np.ascontiguousarray(grad, dtype=np.float64)
     rc = lib.or_coupled_paths(kind, c0, int(y_exp), int(max_steps), cv, grid_n, _ptr(grad), n,
-                              _ptr(xs), _ptr(ys), int(n_paths), float(h), int(seed), int(tag),
+                              _ptr(xs), _ptr(ys), _ptr(zs), int(n_paths), float(h), int(seed),
+                              int(tag),
                               _ptr(out["phi_f"]), _ptr(out["xi_f"]), _ptr(out["steps_f"]),
                               _ptr(out["phi_c"]), _ptr(out["xi_c"]), _ptr(out["steps_c"]))
     if rc != 0:
         raise RuntimeError("or_coupled_paths failed")
     return {k: v.reshape(n, n_paths) for k, v in out.items()}
+
+
+# ---------------------------------------------------------------------------
+# Multilevel Monte Carlo on top of the coupled paths (the variant the paper
+# names as future work, Sec. 1 and Sec. 7).
+# ---------------------------------------------------------------------------
+def mlmc_allocation(var_mean, cost_mean, target_rmse):
+    """Sample counts of a multilevel estimator: minimise sum_l N_l C_l subject
+    to sum_l V_l / N_l = eps^2 / 2.  Stationarity of the Lagrangian gives
+    N_l = mu sqrt(V_l / C_l); the constraint fixes mu = 2 eps^-2
+    sum_k sqrt(V_k C_k).  Rounded up, at least one path."""
+    V = np.asarray(var_mean, dtype=np.float64)
+    C = np.asarray(cost_mean, dtype=np.float64)
+    mu = 2.0 / target_rmse**2 * np.sum(np.sqrt(V * C))
+    return np.maximum(np.ceil(mu * np.sqrt(V / C)), 1.0).astype(np.int64)
+
+
+def mlmc_levels(kind, nodes, dt0, counts, seed=1234, tag_base=0, cv=CV_NONE, grad=None,
+                grid_n=0, controlled=False):
+    """Per-node means, variances (N-1) and costs (exit indices per sample) of
+    the multilevel levels with the given counts: level 0 is Algorithm 1 at
+    dt0 (stream tag_base), level l >= 1 the coupled difference of a path at
+    dt0 / 2^l and one at dt0 / 2^(l-1) (stream tag_base + l).  The score is
+    phi, or phi + xi when `controlled`.  Returns arrays (levels, nodes)."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    m, v, c = [], [], []
+    for l, N in enumerate(counts):
+        if l == 0:
+            r = estimate_nodes(kind, nodes, int(N), dt0, seed=seed, tag=tag_base, cv=cv, grad=grad,
+                               grid_n=grid_n)
+            s = r["phi"] + r["xi"] if controlled else r["phi"]
+            cost = r["steps"].astype(np.float64)
+        else:
+            r = coupled_paths(kind, nodes, int(N), dt0 / 2.0 ** (l - 1), seed=seed,
+                              tag=tag_base + l, cv=cv, grad=grad, grid_n=grid_n)
+            sf = r["phi_f"] + r["xi_f"] if controlled else r["phi_f"]
+            sc = r["phi_c"] + r["xi_c"] if controlled else r["phi_c"]
+            s = sf - sc
+            cost = (r["steps_f"] + r["steps_c"]).astype(np.float64)
+        m.append(s.mean(axis=1))
+        v.append(s.var(axis=1, ddof=1))
+        c.append(cost.mean(axis=1))
+    return np.array(m), np.array(v), np.array(c)
+
+
+def mlmc_combine(m, v, counts, alpha=1.0):
+    """The multilevel estimate sum_l m_l with variance sum_l v_l / N_l, and
+    the Richardson (Talay-Tubaro) extrapolation on the finest pair: with
+    E[phi_h] = u + c h^alpha + ..., the finest correction m_L estimates
+    c h_L^alpha (2^alpha - 1), so u ~ estimate + m_L / (2^alpha - 1)."""
+    m = np.asarray(m, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    N = np.asarray(counts, dtype=np.float64)[:, None]
+    r = 2.0 ** alpha
+    est = m.sum(axis=0)
+    var = (v / N).sum(axis=0)
+    ext = est + m[-1] / (r - 1.0)
+    ext_var = var - v[-1] / N[-1] + (r / (r - 1.0)) ** 2 * v[-1] / N[-1]
+    return {"estimate": est, "variance": var, "extrapolated": ext, "extrap_variance": ext_var}

@@ -452,13 +452,13 @@ static void or_run_path(const or_problem* pb, const double* x0, double h, uint64
 /* Per-path outputs indexed node * n_paths + path; max_steps caps each path. */
 int or_coupled_paths(int kind, double c0, int y_exp, int64_t max_steps, int cv_mode, int grid_n,
                      const double* grad, int64_t n_nodes, const double* xs, const double* ys,
-                     int64_t n_paths, double h, uint64_t seed, uint32_t tag, double* phi_f,
-                     double* xi_f, int64_t* steps_f, double* phi_c, double* xi_c,
+                     const double* zs, int64_t n_paths, double h, uint64_t seed, uint32_t tag,
+                     double* phi_f, double* xi_f, int64_t* steps_f, double* phi_c, double* xi_c,
                      int64_t* steps_c) {
   or_problem pb = {kind, c0, y_exp, max_steps, cv_mode, grid_n, grad};
-  if (or_problem_dim(kind) != 2) return -1;
+  if (or_problem_dim(kind) == 3 && zs == NULL) return -1;
   for (int64_t i = 0; i < n_nodes; ++i) {
-    double x0[3] = {xs[i], ys[i], 0.0};
+    double x0[3] = {xs[i], ys[i], zs ? zs[i] : 0.0};
     for (int64_t p = 0; p < n_paths; ++p) {
       or_path f, c;
       or_run_path(&pb, x0, 0.5 * h, seed, tag, (uint32_t)i, (uint32_t)p, 0, &f);

@@ -970,41 +970,23 @@ int pdd_records_merge(uint64_t* dst, const uint64_t* src, int64_t n_nodes) {
   return PDD_OK;
 }
 
-int pdd_estimate_coupled(pdd_problem* p, const pdd_estimate_args* a, pdd_node_stats* out_fine,
-                         pdd_node_stats* out_diff) {
-  if (!p || !a || !out_fine || !out_diff) {
-    set_error("pdd_estimate_coupled: NULL argument");
-    return PDD_ERR_INVALID;
-  }
-  if (p->dim != 2 || p->desc.precision != PDD_PATH_FP32) {
-    set_error("pdd_estimate_coupled: provided for 2D problems with FP32 paths");
-    return PDD_ERR_INVALID;
-  }
-  LevelPlan lp;
-  int rc = check_level(p, a, out_fine, "pdd_estimate_coupled", 0, &lp);
-  if (rc != PDD_OK) return rc;
-  if (!a->coords_on_device || !out_fine->on_device || !out_diff->on_device) {
-    set_error("pdd_estimate_coupled: coordinates and outputs must be device pointers");
-    return PDD_ERR_INVALID;
-  }
-  if (a->n_nodes == 0) return PDD_OK;
+// One launch of the coupled kernel over pairs path_offset .. path_offset +
+// n_paths - 1 of every node, adding into the fine / difference records rf, rd
+// (device).  The caller holds the context lock and has checked the level.
+static int coupled_launch(pdd_problem* p, const pdd_estimate_args* a, const LevelPlan& lp,
+                          uint64_t path_offset, unsigned long long* rf, unsigned long long* rd,
+                          const char* who) {
+  pdd_ctx* c = p->ctx;
   const double hf = 0.5 * a->dt, hc = a->dt;
   auto steps_cap = [&](double h) -> int {
     int64_t ms = p->desc.max_steps;
     if (ms <= 0) ms = (int64_t)std::min(2.0e9, std::ceil(100.0 / h));
     return (int)std::min<int64_t>(ms, 2000000000ll);
   };
-  pdd_ctx* c = p->ctx;
-  std::lock_guard<std::mutex> lk(c->mu);
-  DeviceGuard g(c->device);
   const size_t n = (size_t)a->n_nodes;
-  const size_t rec_bytes = n * kAccWords * 8;
-  rc = ensure_workspace(c, 256 + 2 * align_up(rec_bytes, 256));
+  int rc = ensure_workspace(c, 256);
   if (rc != PDD_OK) return rc;
-  char* ws = (char*)c->ws;
-  WsHeader* hdr = (WsHeader*)ws;
-  unsigned long long* rf = (unsigned long long*)(ws + 256);
-  unsigned long long* rd = (unsigned long long*)(ws + 256 + align_up(rec_bytes, 256));
+  WsHeader* hdr = (WsHeader*)c->ws;
   PathArgs pa{};
   pa.cursor = &hdr->cursor;
   pa.err = &hdr->err;
@@ -1021,7 +1003,7 @@ int pdd_estimate_coupled(pdd_problem* p, const pdd_estimate_args* a, pdd_node_st
     const double h = l == 0 ? hf : hc;
     sg.cx = a->coords[0];
     sg.cy = a->coords[1];
-    sg.cz = a->coords[0];
+    sg.cz = p->dim == 3 ? a->coords[2] : a->coords[0];
     sg.begin = 0;
     sg.total = pa.total;
     sg.n_paths = (unsigned long long)a->n_paths;
@@ -1036,18 +1018,85 @@ int pdd_estimate_coupled(pdd_problem* p, const pdd_estimate_args* a, pdd_node_st
     sg.h = h;
     sg.sqrt_h = std::sqrt(h);
     sg.thr0 = c0 * sg.sqrt_h;
-    sg.path_off = 0;
+    sg.path_off = (uint32_t)path_offset;
     sg.key0 = (uint32_t)a->seed;
     sg.key1 = a->stream_tag;
     sg.seed_hi = (uint32_t)(a->seed >> 32);
     sg.grid_n = lp.grid_n;
     sg.max_steps = steps_cap(h);
   }
-  PDD_CUDA(cudaMemsetAsync(ws, 0, 256 + 2 * align_up(rec_bytes, 256), c->stream),
-           "cudaMemsetAsync");
+  PDD_CUDA(cudaMemsetAsync(hdr, 0, 256, c->stream), "cudaMemsetAsync");
   int blocks = 0;
-  PDD_CUDA(launch_coupled(p->desc.kind, lp.cv, pa, c->num_sms, c->stream, &blocks),
-           "coupled kernel launch");
+  char what[96];
+  snprintf(what, sizeof(what), "%s: coupled kernel launch", who);
+  PDD_CUDA(launch_coupled(p->desc.kind, lp.cv, pa, c->num_sms, c->stream, &blocks), what);
+  c->launches += 1;
+  return PDD_OK;
+}
+
+// Read the launch header (synchronising the context stream) and turn its
+// error bits into a status.
+static int coupled_status(pdd_ctx* c, const char* who) {
+  WsHeader h{};
+  PDD_CUDA(cudaMemcpyAsync(&h, c->ws, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
+           "cudaMemcpyAsync(header)");
+  PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (h.err & kErrOverflow) {
+    set_error("%s: a score left the fixed-point range |score| < 32768", who);
+    return PDD_ERR_OVERFLOW;
+  }
+  if (h.trunc_total > 0) {
+    set_error("%s: %llu paths hit max_steps", who, h.trunc_total);
+    return PDD_WARN_TRUNCATED;
+  }
+  return PDD_OK;
+}
+
+static int coupled_check(pdd_problem* p, const pdd_estimate_args* a, LevelPlan* lp,
+                         const char* who) {
+  if (p->desc.precision != PDD_PATH_FP32) {
+    set_error("%s: provided for FP32 paths", who);
+    return PDD_ERR_INVALID;
+  }
+  pdd_node_stats dummy{};
+  dummy.on_device = 1;
+  int rc = check_level(p, a, &dummy, who, 0, lp);
+  if (rc != PDD_OK) return rc;
+  if (!a->coords_on_device) {
+    set_error("%s: coordinates must be device pointers", who);
+    return PDD_ERR_INVALID;
+  }
+  return PDD_OK;
+}
+
+int pdd_estimate_coupled(pdd_problem* p, const pdd_estimate_args* a, pdd_node_stats* out_fine,
+                         pdd_node_stats* out_diff) {
+  const char* who = "pdd_estimate_coupled";
+  if (!p || !a || !out_fine || !out_diff) {
+    set_error("%s: NULL argument", who);
+    return PDD_ERR_INVALID;
+  }
+  LevelPlan lp;
+  int rc = coupled_check(p, a, &lp, who);
+  if (rc != PDD_OK) return rc;
+  if (!out_fine->on_device || !out_diff->on_device) {
+    set_error("%s: outputs must be device pointers", who);
+    return PDD_ERR_INVALID;
+  }
+  if (a->n_nodes == 0) return PDD_OK;
+  pdd_ctx* c = p->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  const size_t n = (size_t)a->n_nodes;
+  const size_t rec_bytes = align_up(n * kAccWords * 8, 256);
+  rc = ensure_workspace(c, 256 + 2 * rec_bytes);
+  if (rc != PDD_OK) return rc;
+  char* ws = (char*)c->ws;
+  unsigned long long* rf = (unsigned long long*)(ws + 256);
+  unsigned long long* rd = (unsigned long long*)(ws + 256 + rec_bytes);
+  PDD_CUDA(cudaMemsetAsync(ws + 256, 0, 2 * rec_bytes, c->stream), "cudaMemsetAsync");
+  rc = coupled_launch(p, a, lp, 0, rf, rd, who);
+  if (rc != PDD_OK) return rc;
   const double kappa = a->kappa > 0.0 ? a->kappa : 1.0;
   pdd_node_stats* outs[2] = {out_fine, out_diff};
   unsigned long long* recs[2] = {rf, rd};
@@ -1058,21 +1107,38 @@ int pdd_estimate_coupled(pdd_problem* p, const pdd_estimate_args* a, pdd_node_st
                       (unsigned long long*)o.n_paths, (unsigned long long*)o.n_truncated};
     PDD_CUDA(launch_finalize(recs[l], (uint32_t)n, kappa, sp, c->stream), "finalize launch");
   }
-  c->launches += 3;
+  c->launches += 2;
   if (a->flags & PDD_FLAG_ASYNC) return PDD_OK;
-  WsHeader h{};
-  PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
-           "cudaMemcpyAsync(header)");
-  PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-  if (h.err & kErrOverflow) {
-    set_error("pdd_estimate_coupled: a score left the fixed-point range |score| < 32768");
-    return PDD_ERR_OVERFLOW;
+  return coupled_status(c, who);
+}
+
+int pdd_accumulate_coupled(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_offset,
+                           uint64_t* rec_fine, uint64_t* rec_diff) {
+  const char* who = "pdd_accumulate_coupled";
+  if (!p || !a || !rec_fine || !rec_diff) {
+    set_error("%s: NULL argument", who);
+    return PDD_ERR_INVALID;
   }
-  if (h.trunc_total > 0) {
-    set_error("pdd_estimate_coupled: %llu paths hit max_steps", h.trunc_total);
-    return PDD_WARN_TRUNCATED;
+  LevelPlan lp;
+  int rc = coupled_check(p, a, &lp, who);
+  if (rc != PDD_OK) return rc;
+  if (a->flags & PDD_FLAG_EMIT_PATHS) {
+    set_error("%s: per-path output is not available here", who);
+    return PDD_ERR_INVALID;
   }
-  return PDD_OK;
+  if (path_offset + (uint64_t)a->n_paths > (1ull << 32)) {
+    set_error("%s: path indices beyond 2^32", who);
+    return PDD_ERR_INVALID;
+  }
+  if (a->n_nodes == 0) return PDD_OK;
+  pdd_ctx* c = p->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  rc = coupled_launch(p, a, lp, path_offset, (unsigned long long*)rec_fine,
+                      (unsigned long long*)rec_diff, who);
+  if (rc != PDD_OK) return rc;
+  if (a->flags & PDD_FLAG_ASYNC) return PDD_OK;
+  return coupled_status(c, who);
 }
 
 int pdd_ctx_set_launch(pdd_ctx* c, int block_threads, int max_blocks) {

@@ -17,6 +17,9 @@ static_assert(kAccWords == PDD_RECORD_WORDS, "node record size");
 constexpr unsigned long long kWarpBatch = 32;  // path indices a warp takes per cursor grab
 
 constexpr int kMaxSegments = 128;          // segments (levels / requests) per launch
+// Launches whose segments hold at most this many node records in total keep a
+// per-block copy of the records in shared memory (68 KB with padding).
+constexpr uint32_t kCacheMaxNodes = 512;
 
 // One segment of a launch: n_nodes x n_paths paths with their own nodes,
 // time step, control grid, random-stream key and output records.
@@ -40,6 +43,7 @@ struct SegArgs {
   double sqrt_h;
   double thr0;                 // c0 sqrt(h)
   uint32_t path_off;           // first path index of the segment
+  uint32_t cache_base;         // first shared-memory record slot of the segment's nodes
   uint32_t key0, key1, seed_hi;
   int grid_n;
   int max_steps;
@@ -56,6 +60,8 @@ struct PathArgs {
   int max_blocks;              // 0 = occupancy x SM count
   int block_threads;           // 0 = default (256)
   int n_segs;                  // 1 .. kMaxSegments; segments in increasing `begin`
+  uint32_t cache_nodes;        // record slots cached in shared memory per block (0: none);
+                               // set by the launchers
   SegArgs seg[kMaxSegments];
 };
 
@@ -100,7 +106,7 @@ cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int
 // Resident blocks per SM of the path kernel of (kind, precision, cv, multi) at
 // `threads` threads per block.
 cudaError_t occupancy_paths(int kind, int precision, int cv, bool multi, int threads, int* occ);
-// Coupled fine (seg[0]) / coarse (seg[1]) pairs, 2D problems, FP32 paths.
+// Coupled fine (seg[0]) / coarse (seg[1]) pairs, FP32 paths (2D and 3D problems).
 cudaError_t launch_coupled(int kind, int cv, const PathArgs& a, int num_sms, cudaStream_t st,
                            int* blocks);
 cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, double kappa,

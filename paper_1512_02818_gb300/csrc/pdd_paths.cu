@@ -192,10 +192,12 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
 }
 
 // Exact fixed-point accumulation of one path's (phi, psi = phi + xi, k) into a
-// node record.
+// node record (global, or the block's shared-memory copy), and of k into the
+// launch's step counter `steps` when there is one.
 template <class T>
-__device__ __forceinline__ void accumulate(const PathArgs& a, unsigned long long* w, T phi, T psi,
-                                           int k_steps, bool trunc) {
+__device__ __forceinline__ void accumulate(const PathArgs& a, unsigned long long* w,
+                                           unsigned long long* steps, T phi, T psi, int k_steps,
+                                           bool trunc) {
   long long qa, qb;
   const bool ok = to_fixed(phi, qa) & to_fixed(psi, qb);
   if (!ok) atomicOr(a.err, kErrOverflow);
@@ -212,7 +214,69 @@ __device__ __forceinline__ void accumulate(const PathArgs& a, unsigned long long
     atomicAdd(w + 15, 1ull);
     atomicAdd(a.trunc_total, 1ull);
   }
-  if (a.steps_total != nullptr) atomicAdd(a.steps_total, k);
+  if (steps != nullptr) atomicAdd(steps, k);
+}
+
+// Block-level record cache.  When the launch's segments hold at most
+// kCacheMaxNodes node records, every block keeps its own copy of them in
+// shared memory: exits add into the copy with shared-memory atomics (exits of
+// different nodes no longer meet on a few cache lines of L2), and once all
+// warps of the block have finished the block adds its non-empty records into
+// the global ones (128-bit adds with carry: the same exact sums).  Slot
+// seg.cache_base + node holds the record of `node` of segment `seg`; the word
+// after the last slot counts the block's exit indices for a.steps_total.
+extern __shared__ unsigned long long s_cache[];
+// Slot stride in 64-bit words: one word of padding per record, so the same
+// word of consecutive slots falls in different shared-memory banks.
+constexpr uint32_t kCacheStride = kAccWords + 1;
+
+__device__ __forceinline__ void cache_init(const PathArgs& a) {
+  if (a.cache_nodes == 0) return;
+  const uint32_t words = a.cache_nodes * kCacheStride + 1;
+  for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) s_cache[i] = 0ull;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void cache_flush(const PathArgs& a) {
+  if (a.cache_nodes == 0) return;
+  __syncthreads();
+  const uint32_t pairs = a.cache_nodes * (kAccWords / 2);
+  for (uint32_t i = threadIdx.x; i < pairs; i += blockDim.x) {
+    const uint32_t slot = i / (kAccWords / 2), q = i % (kAccWords / 2);
+    const unsigned long long* s = s_cache + (size_t)slot * kCacheStride;
+    if (s[14] == 0ull) continue;  // no path of this node ended in this block
+    int lo = 0, hi = a.n_segs - 1;  // last segment whose cache_base <= slot
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.seg[mid].cache_base <= slot) lo = mid;
+      else hi = mid - 1;
+    }
+    const SegArgs& sg = a.seg[lo];
+    unsigned long long* g = sg.acc + (size_t)(slot - sg.cache_base) * kAccWords;
+    if (q < 7) {
+      if ((s[2 * q] | s[2 * q + 1]) != 0ull) atomic_add_u128(g + 2 * q, s[2 * q], s[2 * q + 1]);
+    } else {
+      atomicAdd(g + 14, s[14]);
+      if (s[15] != 0ull) atomicAdd(g + 15, s[15]);
+    }
+  }
+  if (threadIdx.x == 0 && a.steps_total != nullptr) {
+    const unsigned long long st = s_cache[(size_t)a.cache_nodes * kCacheStride];
+    if (st != 0ull) atomicAdd(a.steps_total, st);
+  }
+}
+
+// Add one path into the record of `node` of segment `sg` (cached or global).
+template <class T>
+__device__ __forceinline__ void record_path(const PathArgs& a, const SegArgs& sg, uint32_t node,
+                                            T phi, T psi, int k_steps, bool trunc) {
+  if (a.cache_nodes != 0) {
+    accumulate(a, s_cache + (size_t)(sg.cache_base + node) * kCacheStride,
+               a.steps_total != nullptr ? s_cache + (size_t)a.cache_nodes * kCacheStride : nullptr,
+               phi, psi, k_steps, trunc);
+  } else {
+    accumulate(a, sg.acc + (size_t)node * kAccWords, a.steps_total, phi, psi, k_steps, trunc);
+  }
 }
 
 // Exit scoring: X_tau = Pi(X_k), phi = g(X_tau) Y + Z, and xi.
@@ -231,7 +295,7 @@ __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T
   T phi, xi;
   score_path<P, T, D>(s, phi, xi);
   const SegArgs& sg = a.seg[MULTI ? s.seg : 0];
-  accumulate(a, sg.acc + (size_t)s.node * kAccWords, phi, phi + xi, s.k, trunc);
+  record_path(a, sg, s.node, phi, phi + xi, s.k, trunc);
   if (sg.emit_phi != nullptr) {
     const size_t i = (size_t)s.node * sg.emit_stride + s.path;
     sg.emit_phi[i] = (float)phi;
@@ -274,6 +338,101 @@ __device__ __forceinline__ bool refill(const PathArgs& a, PathState<T>& s, LaneS
   return __ballot_sync(kFull, active) != 0u;
 }
 
+// Per-warp exit ring.  A lane whose path has ended parks the path's final
+// state (X, Y, Z, xi, k, node, path, segment | truncated) in its warp's ring
+// in shared memory and takes a new path at once; whenever 32 exits are
+// parked, the whole warp scores and records them, one per lane.  Exit work
+// (projection, g, fixed-point conversion, the record's 13 atomic adds) thus
+// runs with all lanes busy instead of one lane at a time while the rest of
+// the warp waits.  Rings follow the record cache in dynamic shared memory.
+constexpr uint32_t kRing = 64;  // entries per warp (>= 2 x 32: a full batch plus one iteration)
+template <class T, int D>
+struct ExitRing {
+  static constexpr size_t kBytes = kRing * ((D + 3) * sizeof(T) + 4 * sizeof(uint32_t));
+  T* f;         // (D + 3) x kRing: X_0 .. X_(D-1), Y, Z, xi
+  uint32_t* u;  // 4 x kRing: k, node, path, segment | truncated << 31
+};
+
+__host__ __device__ __forceinline__ size_t cache_bytes(uint32_t cache_nodes) {
+  if (cache_nodes == 0) return 0;
+  return (((size_t)cache_nodes * (kAccWords + 1) + 1) * 8 + 15) / 16 * 16;
+}
+
+template <class T, int D>
+__device__ __forceinline__ ExitRing<T, D> ring_of_warp(const PathArgs& a) {
+  char* base = (char*)s_cache + cache_bytes(a.cache_nodes) +
+               (size_t)(threadIdx.x >> 5) * ExitRing<T, D>::kBytes;
+  ExitRing<T, D> r;
+  r.f = (T*)base;
+  r.u = (uint32_t*)(base + kRing * (D + 3) * sizeof(T));
+  return r;
+}
+
+template <class T, int D>
+__device__ __forceinline__ void ring_put(const ExitRing<T, D>& r, uint32_t j,
+                                         const PathState<T>& s, bool trunc) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) r.f[d * kRing + j] = s.x[d];
+  r.f[D * kRing + j] = s.Y;
+  r.f[(D + 1) * kRing + j] = s.Z - s.Zc;
+  r.f[(D + 2) * kRing + j] = s.XI - s.XIc;
+  r.u[j] = (uint32_t)s.k;
+  r.u[kRing + j] = s.node;
+  r.u[2 * kRing + j] = s.path;
+  r.u[3 * kRing + j] = s.seg | (trunc ? 0x80000000u : 0u);
+}
+
+// Score and record `count` (<= 32) parked exits starting at ring slot `first`.
+template <class P, class T, int D, bool MULTI>
+__device__ __forceinline__ void ring_drain(const PathArgs& a, const ExitRing<T, D>& r,
+                                           uint32_t first, uint32_t count) {
+  __syncwarp();
+  const uint32_t lane = threadIdx.x & 31u;
+  if (lane < count) {
+    const uint32_t j = (first + lane) & (kRing - 1);
+    PathState<T> e;
+    e.x[0] = e.x[1] = e.x[2] = T(0);
+#pragma unroll
+    for (int d = 0; d < D; ++d) e.x[d] = r.f[d * kRing + j];
+    e.Y = r.f[D * kRing + j];
+    e.Z = r.f[(D + 1) * kRing + j];
+    e.XI = r.f[(D + 2) * kRing + j];
+    e.Zc = e.XIc = T(0);
+    e.k = (int)r.u[j];
+    e.node = r.u[kRing + j];
+    e.path = r.u[2 * kRing + j];
+    const uint32_t st = r.u[3 * kRing + j];
+    e.seg = st & 0x7FFFFFFFu;
+    finish_path<P, T, D, MULTI>(a, e, (st >> 31) != 0u);
+  }
+  __syncwarp();
+}
+
+// Warp-uniform ring cursor: `head` counts parked exits, `held` those not yet
+// drained.
+struct RingCursor {
+  uint32_t head = 0, held = 0;
+};
+
+// Park the exits of this iteration (`done` lanes) and drain a full batch.
+template <class P, class T, int D, bool MULTI>
+__device__ __forceinline__ void ring_exit(const PathArgs& a, const ExitRing<T, D>& r,
+                                          RingCursor& c, const PathState<T>& s, bool done,
+                                          bool trunc) {
+  const unsigned m = __ballot_sync(kFull, done);
+  if (m == 0u) return;
+  if (done) {
+    const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
+    ring_put<T, D>(r, (c.head + __popc(m & lt)) & (kRing - 1), s, trunc);
+  }
+  c.head += __popc(m);
+  c.held += __popc(m);
+  if (c.held >= 32u) {
+    ring_drain<P, T, D, MULTI>(a, r, c.head - c.held, 32u);
+    c.held -= 32u;
+  }
+}
+
 template <class T, int D>
 __device__ __forceinline__ void init_lane(const PathArgs& a, PathState<T>& s, LaneSeg<T>& ls) {
   s.x[0] = s.x[1] = s.x[2] = T(0);
@@ -289,6 +448,9 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_2D)
   PathState<T> s;
   LaneSeg<T> ls;
   init_lane<T, 2>(a, s, ls);
+  cache_init(a);
+  const ExitRing<T, 2> ring = ring_of_warp<T, 2>(a);
+  RingCursor rc;
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
   while (refill<T, 2, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
@@ -311,11 +473,11 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_2D)
       euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
       if (s.k >= ls.max_steps) fin = trunc = true;
     }
-    if (active && fin) {
-      finish_path<P, T, 2, MULTI>(a, s, trunc);
-      active = false;
-    }
+    ring_exit<P, T, 2, MULTI>(a, ring, rc, s, active && fin, trunc);
+    if (fin) active = false;
   }
+  if (rc.held > 0u) ring_drain<P, T, 2, MULTI>(a, ring, rc.head - rc.held, rc.held);
+  cache_flush(a);
 }
 
 // 3D: steps 4j .. 4j+3 use normals 12j .. 12j+11, i.e. Philox blocks 3j,
@@ -328,6 +490,9 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
   PathState<T> s;
   LaneSeg<T> ls;
   init_lane<T, 3>(a, s, ls);
+  cache_init(a);
+  const ExitRing<T, 3> ring = ring_of_warp<T, 3>(a);
+  RingCursor rc;
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
   while (refill<T, 3, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
@@ -375,40 +540,52 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
       euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
       if (s.k >= ls.max_steps) fin = trunc = true;
     }
-    if (active && fin) {
-      finish_path<P, T, 3, MULTI>(a, s, trunc);
-      active = false;
-    }
+    ring_exit<P, T, 3, MULTI>(a, ring, rc, s, active && fin, trunc);
+    if (fin) active = false;
   }
+  if (rc.held > 0u) ring_drain<P, T, 3, MULTI>(a, ring, rc.head - rc.held, rc.held);
+  cache_flush(a);
 }
 
 // ---------------------------------------------------------------------------
-// Multilevel coupling (2D): per lane a fine path at h_f = h/2 on the path's
-// own stream and a coarse path at h driven by the sums of pairs of fine
-// increments.  Iteration j uses Philox block j: fine steps 2j and 2j+1 take
-// the pairs (n0, n1) and (n2, n3); coarse step j takes
-// dW = sqrt(h_f) (n0 + n2, n1 + n3), i.e. dW_c = dW_f(2j) + dW_f(2j+1).
-// Each path has its own exit test; when both have finished the lane adds
+// Multilevel coupling: per lane a fine path at h_f = h/2 on the path's own
+// stream and a coarse path at h driven by the sums of pairs of fine
+// increments, dW_c(m) = dW_f(2m) + dW_f(2m+1).  Iteration j draws the
+// Philox blocks that feed kFine fine steps (2D: block j, normals 4j .. 4j+3,
+// two fine steps; 3D: blocks 3j .. 3j+2, normals 12j .. 12j+11, four fine
+// steps) and the kFine / 2 coarse steps those increments make.  Each path
+// has its own exit test; when both have finished the lane adds
 // (phi_f, phi_f + xi_f) to the fine records (seg[0].acc) and the differences
-// (phi_f - phi_c, psi_f - psi_c) to the difference records (seg[1].acc).
-// seg[0] holds the fine step and the node / path layout, seg[1] the coarse
-// step; emit pointers of seg[0] / seg[1] receive fine / coarse per-path output.
+// (phi_f - phi_c, psi_f - psi_c) with the coarse exit index to the
+// difference records (seg[1].acc).  seg[0] holds the fine step and the node /
+// path layout (path_off included), seg[1] the coarse step; emit pointers of
+// seg[0] / seg[1] receive fine / coarse per-path output.
 // ---------------------------------------------------------------------------
-template <class P, class T, int CV>
-__global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled_2d(
+template <int D>
+struct CoupledShape {
+  static constexpr int kBlocks = D == 2 ? 1 : 3;        // Philox blocks per iteration
+  static constexpr int kNormals = 4 * kBlocks;
+  static constexpr int kFine = kNormals / D;            // fine steps per iteration
+  static constexpr int kCoarse = kFine / 2;
+};
+
+template <class P, class T, int CV, int D>
+__global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled(
     const __grid_constant__ PathArgs a) {
+  using S = CoupledShape<D>;
   PathState<T> f, c;
   LaneSeg<T> lf, lc;
-  init_lane<T, 2>(a, f, lf);
-  init_lane<T, 2>(a, c, lc);
-  load_seg<T, 2>(a.seg[1], lc);
+  init_lane<T, D>(a, f, lf);
+  init_lane<T, D>(a, c, lc);
+  load_seg<T, D>(a.seg[1], lc);
+  cache_init(a);
   bool active = false, exhausted = false;  // active: the pair still has work
   bool af = false, ac = false;             // fine / coarse path running
   bool tf = false, tc = false;             // truncated
   T phif = T(0), xif = T(0), phic = T(0), xic = T(0);
   uint32_t j = 0;
   unsigned long long bnext = 0, bend = 0;
-  while (refill<T, 2, false>(a, f, lf, active, bnext, bend, exhausted)) {
+  while (refill<T, D, false>(a, f, lf, active, bnext, bend, exhausted)) {
     if (active && f.k == 0 && !af && !ac) {  // refill has just started a new pair in f
       c = f;
       af = ac = true;
@@ -416,27 +593,22 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled_2d(
       j = 0;
     }
     if (active) {
-      const uint4 w = path_block<false>(a, 0, j, f.path, f.node);
-      T n[4];
-      box_muller(w.x, w.y, n[0], n[1], lf.sqh);
-      box_muller(w.z, w.w, n[2], n[3], lf.sqh);
-      // fine: two steps
+      T n[S::kNormals];
+#pragma unroll
+      for (int b = 0; b < S::kBlocks; ++b) {
+        const uint4 w = path_block<false>(a, 0, S::kBlocks * j + b, f.path, f.node);
+        box_muller(w.x, w.y, n[4 * b], n[4 * b + 1], lf.sqh);
+        box_muller(w.z, w.w, n[4 * b + 2], n[4 * b + 3], lf.sqh);
+      }
       if (af) {
-        if (should_finish<P, T, 2>(f, lf.thr0)) {
-          af = false;
-        } else {
-          T d0[3] = {n[0], n[1], T(0)};
-          euler_step<P, T, 2, CV, false>(a, f, lf, d0);
-          if (f.k >= lf.max_steps) {
-            af = false;
-            tf = true;
-          }
+#pragma unroll
+        for (int q = 0; q < S::kFine; ++q) {
           if (af) {
-            if (should_finish<P, T, 2>(f, lf.thr0)) {
+            if (should_finish<P, T, D>(f, lf.thr0)) {
               af = false;
             } else {
-              T d1[3] = {n[2], n[3], T(0)};
-              euler_step<P, T, 2, CV, false>(a, f, lf, d1);
+              T d[3] = {n[D * q], n[D * q + 1], D == 3 ? n[D * q + 2] : T(0)};
+              euler_step<P, T, D, CV, false>(a, f, lf, d);
               if (f.k >= lf.max_steps) {
                 af = false;
                 tf = true;
@@ -444,29 +616,34 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled_2d(
             }
           }
         }
-        if (!af) score_path<P, T, 2>(f, phif, xif);
+        if (!af) score_path<P, T, D>(f, phif, xif);
       }
-      // coarse: one step on the summed increments
       if (ac) {
-        if (should_finish<P, T, 2>(c, lc.thr0)) {
-          ac = false;
-        } else {
-          T dc[3] = {n[0] + n[2], n[1] + n[3], T(0)};
-          euler_step<P, T, 2, CV, false>(a, c, lc, dc);
-          if (c.k >= lc.max_steps) {
-            ac = false;
-            tc = true;
+#pragma unroll
+        for (int q = 0; q < S::kCoarse; ++q) {
+          if (ac) {
+            if (should_finish<P, T, D>(c, lc.thr0)) {
+              ac = false;
+            } else {
+              const int o = 2 * D * q;  // fine steps 2q and 2q+1 of this iteration
+              T d[3] = {n[o] + n[o + D], n[o + 1] + n[o + D + 1],
+                        D == 3 ? n[o + 2] + n[o + D + 2] : T(0)};
+              euler_step<P, T, D, CV, false>(a, c, lc, d);
+              if (c.k >= lc.max_steps) {
+                ac = false;
+                tc = true;
+              }
+            }
           }
         }
-        if (!ac) score_path<P, T, 2>(c, phic, xic);
+        if (!ac) score_path<P, T, D>(c, phic, xic);
       }
       j += 1;
       if (!af && !ac) {
         const SegArgs& s0 = a.seg[0];
         const SegArgs& s1 = a.seg[1];
-        accumulate(a, s0.acc + (size_t)f.node * kAccWords, phif, phif + xif, f.k, tf);
-        accumulate(a, s1.acc + (size_t)f.node * kAccWords, phif - phic,
-                   (phif + xif) - (phic + xic), c.k, tc);
+        record_path(a, s0, f.node, phif, phif + xif, f.k, tf);
+        record_path(a, s1, f.node, phif - phic, (phif + xif) - (phic + xic), c.k, tc);
         if (s0.emit_phi != nullptr) {
           const size_t i = (size_t)f.node * s0.emit_stride + f.path;
           s0.emit_phi[i] = (float)phif;
@@ -480,50 +657,36 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled_2d(
       }
     }
   }
+  cache_flush(a);
 }
 
-template <class P, class T, int CV>
+template <class P, class T, int CV, int D>
 static cudaError_t launch_coupled_one(const PathArgs& a, int num_sms, cudaStream_t st,
                                       int* blocks) {
-  const int threads = a.block_threads > 0 ? a.block_threads : kBlockThreads;
-  if (threads % 32 != 0 || threads > kMaxBlockThreads) return cudaErrorInvalidValue;
-  static int occ = 0;
-  if (occ == 0) {
-    int v = 0;
-    cudaError_t e =
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, paths_coupled_2d<P, T, CV>, threads, 0);
-    if (e != cudaSuccess) return e;
-    occ = v > 0 ? v : 1;
-  }
-  const unsigned long long warps = (a.total + 31ull) / 32ull;
-  const unsigned long long need = (warps + (threads / 32) - 1) / (threads / 32);
-  unsigned long long nb = (unsigned long long)occ * (unsigned long long)num_sms;
-  if (a.max_blocks > 0 && nb > (unsigned long long)a.max_blocks) nb = a.max_blocks;
-  if (nb > need) nb = need;
-  if (nb < 1) nb = 1;
-  *blocks = (int)nb;
-  paths_coupled_2d<P, T, CV><<<(unsigned)nb, (unsigned)threads, 0, st>>>(a);
-  return cudaGetLastError();
+  static int per_sm[kMaxBlockThreads / 32 + 1] = {0};
+  static int attr = 0;
+  return launch_persistent(paths_coupled<P, T, CV, D>, a, num_sms, st, blocks, 0, &attr, per_sm);
 }
 
-template <class P, class T>
+template <class P, class T, int D>
 static cudaError_t launch_coupled_cv(int cv, const PathArgs& a, int sms, cudaStream_t st,
                                      int* blocks) {
   switch (cv) {
-    case kCvNone: return launch_coupled_one<P, T, kCvNone>(a, sms, st, blocks);
-    case kCvGrid: return launch_coupled_one<P, T, kCvGrid>(a, sms, st, blocks);
-    default: return launch_coupled_one<P, T, kCvExact>(a, sms, st, blocks);
+    case kCvNone: return launch_coupled_one<P, T, kCvNone, D>(a, sms, st, blocks);
+    case kCvGrid: return launch_coupled_one<P, T, kCvGrid, D>(a, sms, st, blocks);
+    default: return launch_coupled_one<P, T, kCvExact, D>(a, sms, st, blocks);
   }
 }
 
 cudaError_t launch_coupled(int kind, int cv, const PathArgs& a, int num_sms, cudaStream_t st,
                            int* blocks) {
   switch (kind) {
-    case 0: return launch_coupled_cv<Cfg0, float>(cv, a, num_sms, st, blocks);
-    case 1: return launch_coupled_cv<Aniso, float>(cv, a, num_sms, st, blocks);
-    case 3: return launch_coupled_cv<Harmonic, float>(cv, a, num_sms, st, blocks);
-    case 4: return launch_coupled_cv<PaperEx, float>(cv, a, num_sms, st, blocks);
-    default: return cudaErrorInvalidValue;  // 3D coupling is not provided
+    case 0: return launch_coupled_cv<Cfg0, float, 2>(cv, a, num_sms, st, blocks);
+    case 1: return launch_coupled_cv<Aniso, float, 2>(cv, a, num_sms, st, blocks);
+    case 2: return launch_coupled_cv<Cube3, float, 3>(cv, a, num_sms, st, blocks);
+    case 3: return launch_coupled_cv<Harmonic, float, 2>(cv, a, num_sms, st, blocks);
+    case 4: return launch_coupled_cv<PaperEx, float, 2>(cv, a, num_sms, st, blocks);
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -568,23 +731,55 @@ __global__ void finalize_nodes(const unsigned long long* __restrict__ acc, uint3
 // ---------------------------------------------------------------------------
 // Launch dispatch.
 // ---------------------------------------------------------------------------
-template <class P, class T, int CV, bool MULTI>
-static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, int* blocks) {
-  void (*kern)(PathArgs);
-  if constexpr (P::kDim == 3)
-    kern = paths_3d<P, T, CV, MULTI>;
-  else
-    kern = paths_2d<P, T, CV, MULTI>;
-  const int threads = a.block_threads > 0 ? a.block_threads : kBlockThreads;
+// Shared-memory record slots of a launch (the segments' nodes in segment
+// order) when they fit kCacheMaxNodes; returns the dynamic shared memory the
+// cache needs (0: no cache).
+static size_t plan_cache(PathArgs& b) {
+  unsigned long long tot = 0;
+  for (int i = 0; i < b.n_segs; ++i) tot += b.seg[i].n_nodes;
+  b.cache_nodes = 0;
+  if (tot == 0 || tot > kCacheMaxNodes) return 0;
+  uint32_t base = 0;
+  for (int i = 0; i < b.n_segs; ++i) {
+    b.seg[i].cache_base = base;
+    base += (uint32_t)b.seg[i].n_nodes;
+  }
+  b.cache_nodes = base;
+  return cache_bytes(base);
+}
+constexpr int kCacheBlockThreads = 512;  // default block size of cached launches
+
+// Persistent launch of `kern` over the flat index space of `a`: occupancy x
+// SM count blocks (at most one warp per 32 paths), with the record cache
+// when the launch's nodes fit it and `ring_per_warp` bytes of exit ring per
+// warp.  `attr_set` / `occ_cache` are the kernel's own (static) state: the
+// dynamic shared memory limit set so far and the occupancy per block size
+// without the cache.
+template <class K>
+static cudaError_t launch_persistent(K kern, const PathArgs& a, int num_sms, cudaStream_t st,
+                                     int* blocks, size_t ring_per_warp, int* attr_set,
+                                     int* occ_cache) {
+  PathArgs b = a;
+  const size_t cache = plan_cache(b);
+  const int threads =
+      a.block_threads > 0 ? a.block_threads : (cache > 0 ? kCacheBlockThreads : kBlockThreads);
   if (threads % 32 != 0 || threads > kMaxBlockThreads) return cudaErrorInvalidValue;
-  // occupancy of this instantiation per block size (same for every device here)
-  static int per_sm[kMaxBlockThreads / 32 + 1] = {0};
-  int& occ = per_sm[threads / 32];
-  if (occ == 0) {
+  const size_t smem = cache + (size_t)(threads / 32) * ring_per_warp;
+  if (smem > 48u * 1024u && (int)smem > *attr_set) {
+    const int lim = (int)(cache_bytes(kCacheMaxNodes) + (kMaxBlockThreads / 32) * ring_per_warp);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    *attr_set = lim;
+  }
+  int occ = 0;
+  if (cache == 0 && occ_cache[threads / 32] != 0) {
+    occ = occ_cache[threads / 32];
+  } else {
     int v = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem);
     if (e != cudaSuccess) return e;
     occ = v > 0 ? v : 1;
+    if (cache == 0) occ_cache[threads / 32] = occ;
   }
   const unsigned long long warps_needed = (a.total + 31ull) / 32ull;
   const unsigned long long blocks_needed =
@@ -594,8 +789,21 @@ static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, i
   if (nb > blocks_needed) nb = blocks_needed;
   if (nb < 1) nb = 1;
   *blocks = (int)nb;
-  kern<<<(unsigned)nb, (unsigned)threads, 0, st>>>(a);
+  kern<<<(unsigned)nb, (unsigned)threads, smem, st>>>(b);
   return cudaGetLastError();
+}
+
+template <class P, class T, int CV, bool MULTI>
+static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, int* blocks) {
+  void (*kern)(PathArgs);
+  if constexpr (P::kDim == 3)
+    kern = paths_3d<P, T, CV, MULTI>;
+  else
+    kern = paths_2d<P, T, CV, MULTI>;
+  static int per_sm[kMaxBlockThreads / 32 + 1] = {0};
+  static int attr = 0;
+  return launch_persistent(kern, a, num_sms, st, blocks, ExitRing<T, P::kDim>::kBytes, &attr,
+                           per_sm);
 }
 
 template <class P, class T, int CV, bool MULTI>
@@ -605,7 +813,8 @@ static cudaError_t occupancy_one(int threads, int* occ) {
     kern = paths_3d<P, T, CV, MULTI>;
   else
     kern = paths_2d<P, T, CV, MULTI>;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, 0);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      occ, kern, threads, (size_t)(threads / 32) * ExitRing<T, P::kDim>::kBytes);
 }
 
 template <class P, class T, bool MULTI>

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libpdd.so")
 # ---- constants mirrored from include/pdd.h --------------------------------
 PDD_OK, PDD_ERR_INVALID, PDD_ERR_NOMEM, PDD_ERR_CUDA = 0, -1, -2, -3
 PDD_ERR_TIMEOUT, PDD_ERR_BUSY, PDD_ERR_NOT_READY, PDD_ERR_CANCELLED = -4, -5, -6, -7
-PDD_ERR_OVERFLOW, PDD_WARN_TRUNCATED = -8, 1
+PDD_ERR_OVERFLOW, PDD_WARN_TRUNCATED, PDD_WARN_NOT_CONVERGED = -8, 1, 2
 PDD_PROBLEM_CFG0_2D, PDD_PROBLEM_ANISO_2D, PDD_PROBLEM_CUBE_3D, PDD_PROBLEM_HARMONIC_2D = 0, 1, 2, 3
 PDD_PROBLEM_PAPER_EX_2D = 4
 PDD_EXIT_GOBET_MENOZZI, PDD_EXIT_NAIVE = 0, 1
@@ -33,6 +33,7 @@ PDD_MAX_GRIDS = 8
 PDD_FLAG_EMIT_PATHS, PDD_FLAG_ASYNC, PDD_FLAG_GRAPH = 1, 2, 4
 PDD_MAX_LEVELS = 128
 PDD_RECORD_WORDS = 16
+PDD_MLMC_MAX_LEVELS = 16
 
 STAT_FIELDS = ["mean_phi", "var_phi", "mean_cv", "var_cv", "cov_phi_xi", "var_xi", "rho",
                "se_phi", "se_cv", "vr", "pred_speedup", "mean_steps"]
@@ -97,6 +98,27 @@ class ServerDesc(ctypes.Structure):
                 ("quantum_path_steps", ctypes.c_int64), ("device_arena_bytes", ctypes.c_size_t)]
 
 
+class MlmcArgs(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("coords", ctypes.c_void_p * 3),
+                ("grid_id", ctypes.c_int32), ("min_levels", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dt0", ctypes.c_double), ("n_pilot", ctypes.c_int64),
+                ("target_rmse", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("stream_tag_base", ctypes.c_uint32),
+                ("reserved2", ctypes.c_uint32)]
+
+
+class MlmcOut(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_void_p), ("variance", ctypes.c_void_p),
+                ("extrapolated", ctypes.c_void_p), ("extrap_variance", ctypes.c_void_p),
+                ("n_levels", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("n_paths", ctypes.c_int64 * PDD_MLMC_MAX_LEVELS),
+                ("var_mean", ctypes.c_double * PDD_MLMC_MAX_LEVELS),
+                ("cost_mean", ctypes.c_double * PDD_MLMC_MAX_LEVELS),
+                ("corr_rms", ctypes.c_double * PDD_MLMC_MAX_LEVELS),
+                ("bias_estimate", ctypes.c_double), ("path_steps", ctypes.c_int64)]
+
+
 SERVER_STAT_FIELDS = ["submitted", "admitted", "rejected_busy", "rejected_invalid",
                       "rejected_nomem", "completed", "cancelled", "failed", "launches", "pending",
                       "active", "path_steps"]
@@ -148,6 +170,12 @@ _SIGS = [
                                     ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("pdd_estimate_coupled", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
                                             ctypes.POINTER(NodeStats), ctypes.POINTER(NodeStats)]),
+    ("pdd_accumulate_coupled", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
+                                              ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    ("pdd_mlmc_allocate", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double, ctypes.c_void_p]),
+    ("pdd_mlmc", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(MlmcArgs),
+                                ctypes.POINTER(MlmcOut)]),
     ("pdd_server_create", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerDesc),
                                          ctypes.POINTER(ctypes.c_void_p)]),
     ("pdd_submit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
@@ -319,6 +347,29 @@ def pdd_estimate_coupled(problem: int, args: EstimateArgs, out_fine: NodeStats,
                          out_diff: NodeStats) -> int:
     return _check(lib().pdd_estimate_coupled(problem, ctypes.byref(args), ctypes.byref(out_fine),
                                              ctypes.byref(out_diff)))
+
+
+def pdd_accumulate_coupled(problem: int, args: EstimateArgs, path_offset: int, rec_fine_ptr: int,
+                           rec_diff_ptr: int) -> int:
+    return _check(lib().pdd_accumulate_coupled(problem, ctypes.byref(args), path_offset,
+                                               rec_fine_ptr, rec_diff_ptr))
+
+
+def pdd_mlmc_allocate(var_mean, cost_mean, target_rmse: float):
+    """Sample counts of the multilevel levels (host computation in the
+    library); returns (status, counts)."""
+    import numpy as np
+    V = np.ascontiguousarray(var_mean, dtype=np.float64)
+    C = np.ascontiguousarray(cost_mean, dtype=np.float64)
+    N = np.zeros(V.size, dtype=np.int64)
+    st = _check(lib().pdd_mlmc_allocate(V.size, V.ctypes.data, C.ctypes.data, target_rmse,
+                                        N.ctypes.data))
+    return st, N
+
+
+def pdd_mlmc(problem: int, args: MlmcArgs, out: MlmcOut) -> int:
+    """PDD_OK, PDD_WARN_NOT_CONVERGED or PDD_WARN_TRUNCATED; raises on errors."""
+    return _check(lib().pdd_mlmc(problem, ctypes.byref(args), ctypes.byref(out)))
 
 
 def pdd_server_create(ctx: int, desc: ServerDesc | None = None) -> int:
@@ -591,6 +642,48 @@ class Problem:
         args, _, keep = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, 1.0, False,
                                       True, False, False)
         return pdd_accumulate(self.handle, args, path_offset, records.data_ptr())
+
+    def accumulate_coupled(self, nodes, n_paths: int, dt: float, rec_fine, rec_diff,
+                           path_offset: int = 0, grid_id: int = PDD_CV_NONE, seed: int = 1234,
+                           stream_tag: int = 0):
+        """Add coupled pairs path_offset .. path_offset+n_paths-1 of every node
+        into the fine / difference records (int64 CUDA tensors (n_nodes,
+        PDD_RECORD_WORDS))."""
+        args, _, keep = self._prepare(nodes, n_paths, dt, grid_id, seed, stream_tag, 1.0, False,
+                                      True, False, False)
+        return pdd_accumulate_coupled(self.handle, args, path_offset, rec_fine.data_ptr(),
+                                      rec_diff.data_ptr())
+
+    def mlmc(self, nodes, dt0: float, target_rmse: float, grid_id: int = PDD_CV_NONE,
+             min_levels: int = 2, max_levels: int = 8, n_pilot: int = 1000, alpha: float = 1.0,
+             seed: int = 1234, stream_tag_base: int = 0):
+        """Multilevel Monte Carlo estimate of the nodal values (pdd_mlmc).
+        Returns a dict: status, per-node numpy arrays estimate / variance /
+        extrapolated / extrap_variance, and the per-level counts and moments."""
+        import numpy as np
+        torch = _torch()
+        dev = torch.device("cuda", self.ctx.device)
+        nodes = np.asarray(nodes, dtype=np.float32).reshape(-1, self.dim)
+        cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).to(dev)
+                for j in range(self.dim)]
+        n = nodes.shape[0]
+        a = MlmcArgs()
+        a.n_nodes = n
+        for j in range(3):
+            a.coords[j] = cols[j].data_ptr() if j < self.dim else None
+        a.grid_id, a.min_levels, a.max_levels = grid_id, min_levels, max_levels
+        a.dt0, a.n_pilot, a.target_rmse, a.alpha = dt0, n_pilot, target_rmse, alpha
+        a.seed, a.stream_tag_base = seed, stream_tag_base
+        arrs = {k: np.zeros(n) for k in ("estimate", "variance", "extrapolated", "extrap_variance")}
+        o = MlmcOut()
+        for k, v in arrs.items():
+            setattr(o, k, v.ctypes.data)
+        st = pdd_mlmc(self.handle, a, o)
+        L = o.n_levels
+        return dict(status=st, n_levels=L, rounds=o.rounds, bias_estimate=o.bias_estimate,
+                    path_steps=o.path_steps, n_paths=np.array(o.n_paths[:L], dtype=np.int64),
+                    var_mean=np.array(o.var_mean[:L]), cost_mean=np.array(o.cost_mean[:L]),
+                    corr_rms=np.array(o.corr_rms[:L]), **arrs)
 
     def fit_constants(self, nodes, n_paths: int, h_min: float, h_max: float, n_h: int,
                       grid_id: int = PDD_CV_NONE, delta: float = 1.0, q: float = 2.0,
