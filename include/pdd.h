@@ -300,7 +300,9 @@ int pdd_accumulate_coupled(pdd_problem* problem, const pdd_estimate_args* args,
      4. when every level has its N_l: the bias estimate
         b = max(r_L, r_(L-1) / 2^alpha) / (2^alpha - 1), where r_l is the
         node-RMS of m_l,i with the sampling noise v_l,i / N_l removed; stop
-        if b <= eps / sqrt(2), else add a level (up to max_levels).
+        if b <= eps / sqrt(2), else add a level (up to max_levels).  With
+        min_levels == max_levels the levels are fixed (a bias model chose
+        them) and b is only reported.
    Per node: estimate = sum_l m_l,i, variance = sum_l v_l,i / N_l, and the
    Talay-Tubaro (Richardson) extrapolation on the finest pair,
    extrapolated = estimate + m_L,i / (2^alpha - 1), with its variance

@@ -261,9 +261,10 @@ int pdd_mlmc(pdd_problem* p, const pdd_mlmc_args* a, pdd_mlmc_out* out) {
         more = true;
       }
     if (more) continue;
-    // 4. bias test on the finest corrections; add a level if it fails
+    // 4. bias test on the finest corrections; add a level if it fails (with
+    // min_levels == max_levels the levels are fixed and the test only reported)
     bias = fmax(Rl[L], Rl[L - 1] / r2) / (r2 - 1.0);
-    if (bias <= eps / sqrt(2.0)) {
+    if (bias <= eps / sqrt(2.0) || a->min_levels == a->max_levels) {
       converged = !clamped;
       break;
     }
