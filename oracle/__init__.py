@@ -31,6 +31,7 @@ _lib = None
 # the workloads, not by shared code)
 CFG0_2D, ANISO_2D, CUBE_3D, HARMONIC_2D, PAPER_EX_2D = 0, 1, 2, 3, 4
 CV_NONE, CV_GRID, CV_EXACT = 0, 1, 2
+CV_GRID_CELLS16 = 3  # 3D grid as the FP32 paths read it (cell polynomials, binary16 differences)
 GOBET_MENOZZI_C0 = 0.5826  # Algorithm 1, shrinkage constant as printed
 
 STAT_NAMES = [
@@ -76,6 +77,9 @@ def _load():
         lib.or_build_gradient.argtypes = [i32, i32, P, P]
         lib.or_build_gradient.restype = i32
         lib.or_grad_interp.argtypes = [i32, i32, P, P, P]
+        lib.or_grad_interp_cells16.argtypes = [i32, P, P, P]
+        lib.or_round_f16.argtypes = [dbl]
+        lib.or_round_f16.restype = dbl
         lib.or_nstat.restype = i32
         lib.or_node_stats.argtypes = [i64, P, P, P, P, P, dbl, P]
         lib.or_estimate_nodes.argtypes = [i32, dbl, i32, i64, i32, i32, P, i64, P, P, P, i64,
@@ -170,6 +174,21 @@ def grad_interp(dim: int, n: int, grad: np.ndarray, x) -> np.ndarray:
     out = np.zeros(3)
     lib.or_grad_interp(dim, n, _ptr(grad), _ptr(xx), _ptr(out))
     return out[:dim]
+
+
+def grad_interp_cells16(n: int, grad: np.ndarray, x) -> np.ndarray:
+    """3D control-grid gradient through the cell polynomials with binary16
+    difference coefficients (the FP32 paths' representation)."""
+    lib = _load()
+    xx = np.ascontiguousarray(x, dtype=np.float64)[:3].copy()
+    out = np.zeros(3)
+    lib.or_grad_interp_cells16(n, _ptr(np.ascontiguousarray(grad, dtype=np.float64)), _ptr(xx),
+                               _ptr(out))
+    return out
+
+
+def round_f16(x: float) -> float:
+    return _load().or_round_f16(float(x))
 
 
 def problem_dim(kind: int) -> int:

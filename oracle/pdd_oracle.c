@@ -299,10 +299,66 @@ void or_grad_interp(int dim, int n, const double* grad, const double* x, double*
   }
 }
 
+/* Nearest IEEE 754 binary16 value of x (ties to even), returned as a double. */
+/* binary16 keeps 11 significant bits for |x| >= 2^-14 and the fixed quantum  */
+/* 2^-24 below it; results above the largest finite value 65504 overflow to  */
+/* infinity.                                                                 */
+double or_round_f16(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  double ax = fabs(x);
+  int e;
+  frexp(ax, &e);        /* ax = m 2^e, m in [0.5, 1): ulp of a normal = 2^(e - 11) */
+  int q = e - 11;
+  if (q < -24) q = -24; /* subnormal range */
+  double r = ldexp(rint(ldexp(ax, -q)), q); /* rint: ties to even */
+  if (r > 65504.0) r = INFINITY;
+  return copysign(r, x);
+}
+
+/* Gradient of the 3D control grid as the FP32 paths see it: per cell, the   */
+/* trilinear polynomial of every component, g = c000 + c100 fx + c010 fy +   */
+/* c001 fz + c110 fx fy + c101 fx fz + c011 fy fz + c111 fx fy fz, with the  */
+/* coefficients formed from the 8 corner values of the (FP32-rounded) nodal  */
+/* table, c000 kept as is and the seven others rounded to binary16.          */
+void or_grad_interp_cells16(int n, const double* grad, const double* x, double* out) {
+  long i[3];
+  double f[3];
+  for (int a = 0; a < 3; ++a) {
+    double t = x[a] * (double)(n - 1);
+    long c = (long)floor(t);
+    if (c < 0) c = 0;
+    if (c > n - 2) c = n - 2;
+    i[a] = c;
+    f[a] = t - (double)c;
+  }
+  for (int comp = 0; comp < 3; ++comp) {
+    double v[2][2][2]; /* [dz][dy][dx] */
+    for (int dz = 0; dz < 2; ++dz)
+      for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+          long pt = ((i[2] + dz) * (long)n + (i[1] + dy)) * (long)n + (i[0] + dx);
+          v[dz][dy][dx] = grad[pt * 3 + comp];
+        }
+    double c000 = v[0][0][0];
+    double c100 = or_round_f16(v[0][0][1] - c000);
+    double c010 = or_round_f16(v[0][1][0] - c000);
+    double c001 = or_round_f16(v[1][0][0] - c000);
+    double c110 = or_round_f16(v[0][1][1] - v[0][0][1] - v[0][1][0] + c000);
+    double c101 = or_round_f16(v[1][0][1] - v[0][0][1] - v[1][0][0] + c000);
+    double c011 = or_round_f16(v[1][1][0] - v[0][1][0] - v[1][0][0] + c000);
+    double c111 = or_round_f16(v[1][1][1] - v[0][1][1] - v[1][0][1] - v[1][1][0] + v[0][0][1] +
+                               v[0][1][0] + v[1][0][0] - c000);
+    out[comp] = c000 + c100 * f[0] + c010 * f[1] + c001 * f[2] + c110 * f[0] * f[1] +
+                c101 * f[0] * f[2] + c011 * f[1] * f[2] + c111 * f[0] * f[1] * f[2];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* One path of Algorithm 1.                                                  */
 /* ------------------------------------------------------------------------ */
-enum { OR_CV_NONE = 0, OR_CV_GRID = 1, OR_CV_EXACT = 2 };
+/* OR_CV_GRID: multilinear interpolation of the nodal gradient table;        */
+/* OR_CV_GRID_CELLS16: the 3D cell polynomials above (binary16 differences). */
+enum { OR_CV_NONE = 0, OR_CV_GRID = 1, OR_CV_EXACT = 2, OR_CV_GRID_CELLS16 = 3 };
 
 typedef struct {
   int kind;          /* OR_CFG0_2D ... */
@@ -352,6 +408,7 @@ void or_simulate_path(const or_problem* pb, const double* x0, double h, uint64_t
     if (pb->cv_mode != OR_CV_NONE) {
       double gv[3] = {0, 0, 0};
       if (pb->cv_mode == OR_CV_GRID) or_grad_interp(dim, pb->grid_n, pb->grad, X, gv);
+      else if (pb->cv_mode == OR_CV_GRID_CELLS16) or_grad_interp_cells16(pb->grid_n, pb->grad, X, gv);
       else for (int j = 0; j < dim; ++j) gv[j] = o.grad_u[j];
       double dot = 0.0, st2 = 0.0;
       for (int i = 0; i < dim; ++i) dot += gv[i] * sdW[i];
@@ -427,6 +484,7 @@ static void or_run_path(const or_problem* pb, const double* x0, double h, uint64
     if (pb->cv_mode != OR_CV_NONE) {
       double gv[3] = {0, 0, 0};
       if (pb->cv_mode == OR_CV_GRID) or_grad_interp(dim, pb->grid_n, pb->grad, X, gv);
+      else if (pb->cv_mode == OR_CV_GRID_CELLS16) or_grad_interp_cells16(pb->grid_n, pb->grad, X, gv);
       else for (int j = 0; j < dim; ++j) gv[j] = o.grad_u[j];
       double dot = 0.0;
       for (int i = 0; i < dim; ++i) dot += gv[i] * sdW[i];

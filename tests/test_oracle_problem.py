@@ -132,3 +132,65 @@ def test_gradient_table_exact_for_quadratics(oracle_mod, dim, n):
     corner = np.ones(dim)
     assert np.allclose(oracle_mod.grad_interp(dim, n, grad.reshape(-1), corner), exact(corner),
                        rtol=1e-6, atol=1e-6)
+
+
+# ---- the 3D cell table of the FP32 paths (binary16 difference coefficients) --
+def test_round_f16_matches_numpy(oracle_mod):
+    rng = np.random.default_rng(5)
+    mags = np.exp(rng.uniform(np.log(1e-9), np.log(7e4), 20000))
+    xs = list(mags * rng.choice([-1.0, 1.0], mags.size))
+    # exact ties between binary16 neighbours (normal and subnormal), and the overflow edge
+    for e in (-20, -14, -3, 0, 7, 14):
+        ulp = 2.0 ** max(e - 10, -24)
+        for k in (1, 2, 3, 1023):
+            xs.append((2.0**e) + (k + 0.5) * ulp)
+    xs += [65504.0, 65519.99, 65520.0, 2.0**-24, 2.0**-25, 3 * 2.0**-26, 0.0, -0.0]
+    with np.errstate(over="ignore"):
+        ref = np.asarray(xs, dtype=np.float64).astype(np.float16).astype(np.float64)
+    got = np.array([oracle_mod.round_f16(x) for x in xs])
+    assert np.array_equal(got, ref)
+
+
+def test_cells16_exact_for_dyadic_gradients(oracle_mod):
+    """v = x^2 + 3y^2 + 5z^2 + xy + 2yz on 17^3 points: the nodal gradient is exact
+    and all its cell differences are dyadic, so the binary16 cell polynomials
+    reproduce grad v = (2x + y, 6y + x + 2z, 10z + 2y) exactly."""
+    n = 17
+    g = np.linspace(0, 1, n)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    v = X**2 + 3 * Y**2 + 5 * Z**2 + X * Y + 2 * Y * Z
+    grad = oracle_mod.build_gradient(3, v)
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        p = rng.uniform(0, 1, 3)
+        want = np.array([2 * p[0] + p[1], 6 * p[1] + p[0] + 2 * p[2], 10 * p[2] + 2 * p[1]])
+        assert np.allclose(oracle_mod.grad_interp_cells16(n, grad, p), want, rtol=0, atol=1e-13)
+        assert np.allclose(oracle_mod.grad_interp(3, n, grad, p), want, rtol=0, atol=1e-13)
+
+
+def test_cells16_within_the_rounding_bound(oracle_mod):
+    """On a general smooth grid the cell polynomials differ from the exact
+    trilinear interpolation only by the binary16 rounding of the seven
+    difference coefficients: |err| <= sum_j |c_j| 2^-11 |monomial_j| per component."""
+    n = 33
+    v = __import__("paper_1512_02818_gb300.workloads", fromlist=["x"]).control_grid(2, n, 1e-1)
+    grad = oracle_mod.build_gradient(3, v).reshape(n, n, n, 3)
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        p = rng.uniform(0, 1, 3)
+        t = p * (n - 1)
+        i = np.minimum(np.floor(t).astype(int), n - 2)
+        f = t - i
+        c = grad[i[2]:i[2] + 2, i[1]:i[1] + 2, i[0]:i[0] + 2]  # [dz, dy, dx, comp]
+        d = [c[0, 0, 1] - c[0, 0, 0], c[0, 1, 0] - c[0, 0, 0], c[1, 0, 0] - c[0, 0, 0],
+             c[0, 1, 1] - c[0, 0, 1] - c[0, 1, 0] + c[0, 0, 0],
+             c[1, 0, 1] - c[0, 0, 1] - c[1, 0, 0] + c[0, 0, 0],
+             c[1, 1, 0] - c[0, 1, 0] - c[1, 0, 0] + c[0, 0, 0],
+             c[1, 1, 1] - c[0, 1, 1] - c[1, 0, 1] - c[1, 1, 0] + c[0, 0, 1] + c[0, 1, 0]
+             + c[1, 0, 0] - c[0, 0, 0]]
+        mono = [f[0], f[1], f[2], f[0] * f[1], f[0] * f[2], f[1] * f[2], f[0] * f[1] * f[2]]
+        bound = sum(np.abs(dj) * 2.0**-11 * m for dj, m in zip(d, mono)) + 1e-12
+        err = np.abs(oracle_mod.grad_interp_cells16(n, grad.reshape(-1), p)
+                     - oracle_mod.grad_interp(3, n, grad.reshape(-1), p))
+        assert np.all(err <= bound), (err, bound)
+        assert np.any(err > 0) or np.all(bound < 1e-9)
