@@ -738,9 +738,10 @@ int pdd_set_control_grid(pdd_problem* p, int grid_id, const pdd_grid_desc* d) {
   const size_t comps = d->kind == PDD_GRID_VALUES ? 1 : (size_t)dim;
   const size_t count = npts * comps;
   const size_t elt = d->dtype == PDD_DTYPE_F32 ? 4 : 8;
-  // stage the input as FP64 on the device
+  // stage the input as FP64 on the device (plus a flag word for the cell table)
   double* staged = nullptr;
-  PDD_CUDA(cudaMalloc(&staged, count * sizeof(double)), "cudaMalloc(grid staging)");
+  PDD_CUDA(cudaMalloc(&staged, count * sizeof(double) + 16), "cudaMalloc(grid staging)");
+  unsigned* overflow = (unsigned*)(staged + count);
   cudaError_t e = cudaSuccess;
   if (d->dtype == PDD_DTYPE_F64) {
     e = cudaMemcpyAsync(staged, d->data, count * elt,
@@ -761,7 +762,7 @@ int pdd_set_control_grid(pdd_problem* p, int grid_id, const pdd_grid_desc* d) {
   void* table = nullptr;
   const size_t m = (size_t)d->n - 1;
   const size_t ncell = dim == 2 ? m * m : m * m * m;
-  const size_t tbytes = cell_table_offset(d->n, dim) + ncell * (dim == 2 ? 32 : 96);
+  const size_t tbytes = cell_table_offset(d->n, dim) + ncell * (dim == 2 ? 32 : 64);
   if (e == cudaSuccess) e = cudaMalloc(&table, tbytes);
   // cell records are read with 32-byte vector loads: the table must start on a
   // 32-byte boundary (cudaMalloc gives 256; the offset is a multiple of 256)
@@ -776,16 +777,29 @@ int pdd_set_control_grid(pdd_problem* p, int grid_id, const pdd_grid_desc* d) {
                                    : launch_grid_pack(staged, d->n, dim, table, c->stream);
     c->launches += 1;
   }
+  if (e == cudaSuccess) e = cudaMemsetAsync(overflow, 0, sizeof(unsigned), c->stream);
   if (e == cudaSuccess) {
     e = launch_grid_cells(table, d->n, dim, (char*)table + cell_table_offset(d->n, dim),
-                          c->stream);
+                          overflow, c->stream);
     c->launches += 1;
   }
+  unsigned ovf = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&ovf, overflow, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(staged);
   if (e != cudaSuccess) {
     if (table) cudaFree(table);
     return cuda_fail(e, "pdd_set_control_grid");
+  }
+  // FP32 3D paths read binary16 differences: a grid beyond that range would
+  // give them a wrong gradient (such gradients would overflow the scores'
+  // fixed-point range within a few steps anyway)
+  if (ovf != 0 && dim == 3 && p->desc.precision == PDD_PATH_FP32) {
+    cudaFree(table);
+    set_error("pdd_set_control_grid: gradient differences between neighbouring grid points "
+              "exceed 65504 (the binary16 range of the 3D cell table)");
+    return PDD_ERR_INVALID;
   }
   GridSlot& s = p->grids[grid_id];
   if (s.table) cudaFree(s.table);  // the stream was drained above

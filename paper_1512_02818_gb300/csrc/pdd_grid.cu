@@ -3,6 +3,7 @@
 // Sec. 3.1, entering the control variate F = -sigma^T grad v, eq. F:ExactF).
 // Centred differences inside, second-order one-sided differences on the
 // edges, in FP64; stored in FP32 as float2 (2D) or float4 (3D, w = 0).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -56,9 +57,12 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ src, double* __restr
 }
 
 // Multilinear polynomial coefficients of every cell, from the FP32 nodal table
-// (promoted to FP64), rounded to FP32.  Record layouts: see pdd_device.cuh.
+// (promoted to FP64).  2D: FP32 coefficients; 3D: c000 in FP32 and the seven
+// difference coefficients rounded to binary16 (a 64-byte record; `overflow`
+// is set when one of them leaves the binary16 range).  Record layouts: see
+// pdd_device.cuh.
 __global__ void grid_cells_kernel(const void* __restrict__ nodal, int n, int dim,
-                                  float4* __restrict__ cells) {
+                                  float4* __restrict__ cells, unsigned* __restrict__ overflow) {
   const long long m = n - 1;
   const long long ncell = dim == 2 ? m * m : m * m * m;
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -84,23 +88,35 @@ __global__ void grid_cells_kernel(const void* __restrict__ nodal, int n, int dim
     for (int dy = 0; dy < 2; ++dy)
       for (int dx = 0; dx < 2; ++dx)
         g[dz][dy][dx] = G[((iz + dz) * nn + (iy + dy)) * nn + ix + dx];
+  uint32_t w[16] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  unsigned short h[22] = {0};
+  bool bad = false;
   for (int comp = 0; comp < 3; ++comp) {
     auto v = [&](int dx, int dy, int dz) -> double {
       const float4 q = g[dz][dy][dx];
       return comp == 0 ? q.x : (comp == 1 ? q.y : q.z);
     };
     const double c000 = v(0, 0, 0);
-    const double c100 = v(1, 0, 0) - c000;
-    const double c010 = v(0, 1, 0) - c000;
-    const double c001 = v(0, 0, 1) - c000;
-    const double c110 = v(1, 1, 0) - v(1, 0, 0) - v(0, 1, 0) + c000;
-    const double c101 = v(1, 0, 1) - v(1, 0, 0) - v(0, 0, 1) + c000;
-    const double c011 = v(0, 1, 1) - v(0, 1, 0) - v(0, 0, 1) + c000;
-    const double c111 = v(1, 1, 1) - v(1, 1, 0) - v(1, 0, 1) - v(0, 1, 1) + v(1, 0, 0) +
-                        v(0, 1, 0) + v(0, 0, 1) - c000;
-    cells[6 * c + 2 * comp] = make_float4((float)c000, (float)c100, (float)c010, (float)c001);
-    cells[6 * c + 2 * comp + 1] = make_float4((float)c110, (float)c101, (float)c011, (float)c111);
+    const double d[7] = {
+        v(1, 0, 0) - c000,                                  // c100
+        v(0, 1, 0) - c000,                                  // c010
+        v(0, 0, 1) - c000,                                  // c001
+        v(1, 1, 0) - v(1, 0, 0) - v(0, 1, 0) + c000,        // c110
+        v(1, 0, 1) - v(1, 0, 0) - v(0, 0, 1) + c000,        // c101
+        v(0, 1, 1) - v(0, 1, 0) - v(0, 0, 1) + c000,        // c011
+        v(1, 1, 1) - v(1, 1, 0) - v(1, 0, 1) - v(0, 1, 1) + v(1, 0, 0) + v(0, 1, 0) +
+            v(0, 0, 1) - c000};                             // c111
+    w[comp] = __float_as_uint((float)c000);
+    for (int j = 0; j < 7; ++j) {
+      const __half q = __double2half(d[j]);
+      bad |= __hisinf(q) != 0;
+      h[7 * comp + j] = __half_as_ushort(q);
+    }
   }
+  for (int k = 0; k < 11; ++k) w[3 + k] = (uint32_t)h[2 * k] | ((uint32_t)h[2 * k + 1] << 16);
+  uint4* out = (uint4*)cells + 4 * c;
+  for (int k = 0; k < 4; ++k) out[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  if (bad && overflow != nullptr) atomicOr(overflow, 1u);
 }
 
 static unsigned blocks_for(long long count, unsigned threads) {
@@ -128,10 +144,12 @@ cudaError_t launch_f32_to_f64(const float* src, double* dst, size_t count, cudaS
 }  // namespace pdd
 
 namespace pdd {
-cudaError_t launch_grid_cells(const void* nodal, int n, int dim, void* cells, cudaStream_t st) {
+cudaError_t launch_grid_cells(const void* nodal, int n, int dim, void* cells, unsigned* overflow,
+                              cudaStream_t st) {
   const long long m = n - 1;
   const long long ncell = dim == 2 ? m * m : m * m * m;
-  grid_cells_kernel<<<blocks_for(ncell, 256), 256, 0, st>>>(nodal, n, dim, (float4*)cells);
+  grid_cells_kernel<<<blocks_for(ncell, 256), 256, 0, st>>>(nodal, n, dim, (float4*)cells,
+                                                            overflow);
   return cudaGetLastError();
 }
 }  // namespace pdd

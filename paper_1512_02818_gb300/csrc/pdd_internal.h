@@ -115,8 +115,11 @@ cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, dou
 cudaError_t launch_grid_gradient(const double* v, int n, int dim, void* table, cudaStream_t st);
 // Pack D interleaved gradient components (FP64) into float2/float4.
 cudaError_t launch_grid_pack(const double* g, int n, int dim, void* table, cudaStream_t st);
-// Per-cell multilinear coefficients (float4 records) from a nodal table.
-cudaError_t launch_grid_cells(const void* nodal, int n, int dim, void* cells, cudaStream_t st);
+// Per-cell multilinear coefficients from a nodal table (2D: 32-byte FP32
+// records; 3D: 64-byte records with binary16 differences, *overflow set when
+// one leaves the binary16 range).
+cudaError_t launch_grid_cells(const void* nodal, int n, int dim, void* cells, unsigned* overflow,
+                              cudaStream_t st);
 // FP32 -> FP64 copy on the device.
 cudaError_t launch_f32_to_f64(const float* src, double* dst, size_t count, cudaStream_t st);
 

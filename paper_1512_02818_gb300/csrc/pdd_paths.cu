@@ -831,7 +831,7 @@ static cudaError_t occupancy_kind(int kind, int cv, int threads, int* occ) {
   switch (kind) {
     case 0: return occupancy_cv<Cfg0, T, MULTI>(cv, threads, occ);
     case 1: return occupancy_cv<Aniso, T, MULTI>(cv, threads, occ);
-    case 2: return occupancy_cv<Cube3, T, MULTI>(cv, threads, occ);
+    case 2: return occupancy_cv<Cube3, T, true>(cv, threads, occ);  // see launch_kind
     case 4: return occupancy_cv<PaperEx, T, MULTI>(cv, threads, occ);
     default: return occupancy_cv<Harmonic, T, MULTI>(cv, threads, occ);
   }
@@ -861,7 +861,11 @@ static cudaError_t launch_kind(int kind, int cv, const PathArgs& a, int sms, cud
   switch (kind) {
     case 0: return launch_cv<Cfg0, T, MULTI>(cv, a, sms, st, blocks);
     case 1: return launch_cv<Aniso, T, MULTI>(cv, a, sms, st, blocks);
-    case 2: return launch_cv<Cube3, T, MULTI>(cv, a, sms, st, blocks);
+    // 3D launches always run the segment-table build of the kernel: on GB300
+    // it measured 1.43x faster than the single-segment build on one segment
+    // (1.26e11 vs 8.8e10 path-steps/s; ncu showed the single-segment build
+    // stalled on the texture/MIO queues), so the latter is not instantiated
+    case 2: return launch_cv<Cube3, T, true>(cv, a, sms, st, blocks);
     case 4: return launch_cv<PaperEx, T, MULTI>(cv, a, sms, st, blocks);
     default: return launch_cv<Harmonic, T, MULTI>(cv, a, sms, st, blocks);
   }

@@ -100,7 +100,7 @@ def test_coupled_3d_matches_oracle(cv):
     if cv == "grid":
         v = W.control_grid(2, 17, 1e-2)
         prob.set_control_grid(0, v)
-        grad, gid, ocv, gn = oracle.build_gradient(3, v), 0, oracle.CV_GRID, 17
+        grad, gid, ocv, gn = oracle.build_gradient(3, v), 0, oracle.CV_GRID_CELLS16, 17
     N, h = 200, 4e-3
     fine, diff = prob.estimate_coupled(nodes, N, h, grid_id=gid, seed=7, stream_tag=5,
                                        emit_paths=True)

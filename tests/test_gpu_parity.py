@@ -67,6 +67,8 @@ def _run_case(env, case, precision=0):
         gn = grid[0]
         grad = _grid(env, prob, kind, gn, grid[1])
         grid_id, ocv = 0, oracle.CV_GRID
+        if kind == W.CUBE_3D and precision == 0:  # FP32 3D paths read the binary16 cell table
+            ocv = oracle.CV_GRID_CELLS16
     elif cv == "exact":
         grid_id, ocv = pdd.PDD_CV_EXACT, oracle.CV_EXACT
     g = prob.estimate(nodes, n_paths, dt, grid_id=grid_id, seed=1234, stream_tag=7,
@@ -224,3 +226,23 @@ def test_grid_gradient_table_matches_oracle(env):
     # FP32 input values give a table within FP32 rounding of the FP64 one
     assert np.abs(a["xi"].cpu().numpy() - c["xi"].cpu().numpy()).max() < 1e-4
     prob.close()
+
+
+def test_3d_cell_table_range(env):
+    """FP32 3D paths read binary16 difference coefficients: a grid whose
+    neighbouring gradient values differ by more than 65504 is refused for
+    them and accepted for FP64 paths (which read the FP32 nodal table)."""
+    pdd = env["pdd"]
+    n = 9
+    g = np.linspace(0, 1, n)
+    Z, Y, X = np.meshgrid(g, g, g, indexing="ij")
+    v = 1e5 * X**2  # grad_x = 2e5 x: neighbours differ by 2.5e4 ... fine
+    p32 = pdd.Problem(env["ctx"], pdd.PDD_PROBLEM_CUBE_3D)
+    p32.set_control_grid(0, v)
+    with pytest.raises(pdd.PddError) as e:
+        p32.set_control_grid(1, 1e6 * X**2)  # neighbours differ by 2.5e5
+    assert e.value.status == pdd.PDD_ERR_INVALID
+    p64 = pdd.Problem(env["ctx"], pdd.PDD_PROBLEM_CUBE_3D, precision=pdd.PDD_PATH_FP64)
+    p64.set_control_grid(1, 1e6 * X**2)
+    p32.close()
+    p64.close()
