@@ -574,10 +574,61 @@ struct CoupledShape {
   static constexpr int kCoarse = kFine / 2;
 };
 
+// Per-warp ring of finished pairs (the coupled counterpart of ExitRing): the
+// two scores of each path, both exit indices, node, path and truncation
+// flags; drained 32 pairs at a time into the fine and difference records.
+template <class T>
+struct PairRing {
+  static constexpr size_t kBytes = kRing * (4 * sizeof(T) + 5 * sizeof(uint32_t));
+  T* f;         // 4 x kRing: phi_f, xi_f, phi_c, xi_c
+  uint32_t* u;  // 5 x kRing: k_f, k_c, node, path, truncated (bit 0 fine, bit 1 coarse)
+};
+
+template <class T>
+__device__ __forceinline__ PairRing<T> pair_ring_of_warp(const PathArgs& a) {
+  char* base = (char*)s_cache + cache_bytes(a.cache_nodes) +
+               (size_t)(threadIdx.x >> 5) * PairRing<T>::kBytes;
+  PairRing<T> r;
+  r.f = (T*)base;
+  r.u = (uint32_t*)(base + kRing * 4 * sizeof(T));
+  return r;
+}
+
+template <class T>
+__device__ __forceinline__ void pair_drain(const PathArgs& a, const PairRing<T>& r,
+                                           uint32_t first, uint32_t count) {
+  __syncwarp();
+  const uint32_t lane = threadIdx.x & 31u;
+  if (lane < count) {
+    const uint32_t j = (first + lane) & (kRing - 1);
+    const T phif = r.f[j], xif = r.f[kRing + j], phic = r.f[2 * kRing + j],
+            xic = r.f[3 * kRing + j];
+    const int kf = (int)r.u[j], kc = (int)r.u[kRing + j];
+    const uint32_t node = r.u[2 * kRing + j], path = r.u[3 * kRing + j];
+    const uint32_t tr = r.u[4 * kRing + j];
+    const SegArgs& s0 = a.seg[0];
+    const SegArgs& s1 = a.seg[1];
+    record_path(a, s0, node, phif, phif + xif, kf, (tr & 1u) != 0u);
+    record_path(a, s1, node, phif - phic, (phif + xif) - (phic + xic), kc, (tr & 2u) != 0u);
+    if (s0.emit_phi != nullptr) {
+      const size_t i = (size_t)node * s0.emit_stride + path;
+      s0.emit_phi[i] = (float)phif;
+      s0.emit_xi[i] = (float)xif;
+      s0.emit_steps[i] = kf;
+      s1.emit_phi[i] = (float)phic;
+      s1.emit_xi[i] = (float)xic;
+      s1.emit_steps[i] = kc;
+    }
+  }
+  __syncwarp();
+}
+
 template <class P, class T, int CV, int D>
 __global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled(
     const __grid_constant__ PathArgs a) {
   using S = CoupledShape<D>;
+  const PairRing<T> ring = pair_ring_of_warp<T>(a);
+  RingCursor rc;
   PathState<T> f, c;
   LaneSeg<T> lf, lc;
   init_lane<T, D>(a, f, lf);
@@ -644,24 +695,34 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled(
         if (!ac) score_path<P, T, D>(c, phic, xic);
       }
       j += 1;
-      if (!af && !ac) {
-        const SegArgs& s0 = a.seg[0];
-        const SegArgs& s1 = a.seg[1];
-        record_path(a, s0, f.node, phif, phif + xif, f.k, tf);
-        record_path(a, s1, f.node, phif - phic, (phif + xif) - (phic + xic), c.k, tc);
-        if (s0.emit_phi != nullptr) {
-          const size_t i = (size_t)f.node * s0.emit_stride + f.path;
-          s0.emit_phi[i] = (float)phif;
-          s0.emit_xi[i] = (float)xif;
-          s0.emit_steps[i] = f.k;
-          s1.emit_phi[i] = (float)phic;
-          s1.emit_xi[i] = (float)xic;
-          s1.emit_steps[i] = c.k;
-        }
+    }
+    // park finished pairs; drain 32 at a time with the whole warp
+    const bool done = active && !af && !ac;
+    const unsigned m = __ballot_sync(kFull, done);
+    if (m != 0u) {
+      if (done) {
+        const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
+        const uint32_t q = (rc.head + __popc(m & lt)) & (kRing - 1);
+        ring.f[q] = phif;
+        ring.f[kRing + q] = xif;
+        ring.f[2 * kRing + q] = phic;
+        ring.f[3 * kRing + q] = xic;
+        ring.u[q] = (uint32_t)f.k;
+        ring.u[kRing + q] = (uint32_t)c.k;
+        ring.u[2 * kRing + q] = f.node;
+        ring.u[3 * kRing + q] = f.path;
+        ring.u[4 * kRing + q] = (tf ? 1u : 0u) | (tc ? 2u : 0u);
         active = false;
+      }
+      rc.head += __popc(m);
+      rc.held += __popc(m);
+      if (rc.held >= 32u) {
+        pair_drain<T>(a, ring, rc.head - rc.held, 32u);
+        rc.held -= 32u;
       }
     }
   }
+  if (rc.held > 0u) pair_drain<T>(a, ring, rc.head - rc.held, rc.held);
   cache_flush(a);
 }
 
@@ -670,7 +731,8 @@ static cudaError_t launch_coupled_one(const PathArgs& a, int num_sms, cudaStream
                                       int* blocks) {
   static int per_sm[kMaxBlockThreads / 32 + 1] = {0};
   static int attr = 0;
-  return launch_persistent(paths_coupled<P, T, CV, D>, a, num_sms, st, blocks, 0, &attr, per_sm);
+  return launch_persistent(paths_coupled<P, T, CV, D>, a, num_sms, st, blocks,
+                           PairRing<T>::kBytes, &attr, per_sm);
 }
 
 template <class P, class T, int D>

@@ -144,3 +144,36 @@ def test_levels_reject_mixed_exact_and_grid(env):
                               dict(nodes=nodes, n_paths=10, dt=1e-3, grid_id=pdd.PDD_CV_EXACT)])
     assert e.value.status == pdd.PDD_ERR_INVALID
     prob.close()
+
+
+def test_record_cache_boundary(env):
+    """Launches whose nodes fit the per-block shared-memory record cache (at
+    most 512 node records) and launches that add into the global records
+    directly give the same bits: the first 512 of 513 nodes (cache off)
+    against the same 512 nodes alone (cache on), and two levels of 256 nodes
+    (cache on) against 300 + 256 nodes (cache off).  Short paths (dt 1e-2)
+    make many exits per step, so the exit rings drain often."""
+    torch, pdd, ctx = env
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    prob.set_control_grid(0, W.control_grid(0, 65, 1e-2))
+    rng = np.random.default_rng(17)
+    nodes = W.random_interface_nodes(rng, 513)
+    for dt, n_paths in ((1e-2, 3000), (1e-3, 400)):
+        big = prob.estimate(nodes, n_paths, dt, grid_id=0, stream_tag=3, emit_paths=True)
+        small = prob.estimate(nodes[:512], n_paths, dt, grid_id=0, stream_tag=3, emit_paths=True)
+        for f in pdd.STAT_FIELDS + pdd.COUNT_FIELDS:
+            assert np.array_equal(big[f].cpu().numpy()[:512], small[f].cpu().numpy(),
+                                  equal_nan=True), (dt, f)
+        for f in ("phi", "xi", "steps"):
+            assert np.array_equal(big[f].cpu().numpy()[:512], small[f].cpu().numpy()), (dt, f)
+    lv_cached = [dict(nodes=nodes[:256], n_paths=2000, dt=1e-2, grid_id=0, stream_tag=5),
+                 dict(nodes=nodes[256:512], n_paths=1500, dt=2e-3, grid_id=-1, stream_tag=6)]
+    lv_global = [dict(nodes=nodes[:300], n_paths=2000, dt=1e-2, grid_id=0, stream_tag=5),
+                 dict(nodes=nodes[256:512], n_paths=1500, dt=2e-3, grid_id=-1, stream_tag=6)]
+    a = prob.estimate_levels(lv_cached)[1]
+    b = prob.estimate_levels(lv_global)[1]
+    for f in pdd.STAT_FIELDS + pdd.COUNT_FIELDS:
+        assert np.array_equal(a[0][f].cpu().numpy(), b[0][f].cpu().numpy()[:256],
+                              equal_nan=True), f
+        assert np.array_equal(a[1][f].cpu().numpy(), b[1][f].cpu().numpy(), equal_nan=True), f
+    prob.close()
