@@ -50,7 +50,7 @@ ALGO_INSTR = {"plain": 110.0, "cv": 150.0}
 # DRAM bytes (read + write) per launch of the dominant kernel from the ncu
 # capture summarised in profiles/paths_2d_cv_profiling_case.md; None whenever
 # the kernel has changed since that capture.
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES = 909824
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
