@@ -69,13 +69,14 @@ def parse_args():
                     help="keep the library's default launch shape")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 64 of the 256 nodes x 2e4 paths (same kernels)")
-    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit", "mlmc"],
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit", "mlmc", "paper"],
                     default="c1",
                     help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c0: 24 nodes, "
                          "plain, dt 1e-3; fit: Algorithm 3 on the 24 nodes; c2: 3D "
                          "three-level cascade in one launch (CUDA graph); c3: serving with "
                          "Poisson arrivals; c4: anisotropic 2D, FP32 vs FP64 paths; mlmc: "
-                         "multilevel driver at a fixed RMSE vs the single level")
+                         "multilevel driver at a fixed RMSE vs the single level; paper: the "
+                         "paper's example PDE on 18 nodes")
     ap.add_argument("--window", type=float, default=10.0, help="c3: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="c3: arrivals per second")
     return ap.parse_args()
@@ -761,6 +762,64 @@ def run_c0(args):
     return out
 
 
+def run_paper(args):
+    """The paper's example PDE (sigma = sqrt(2) I, b = cos(x+y)(1,1)/(1.1+sin(x+y)),
+    c = (x^2+y^2)/(1.1+sin(x+y)), exact u given) on the assumed domain: the
+    unit square cut into 4 vertical strips, 3 interfaces x 6 nodes = 18
+    nodes; 1e5 paths at dt = 1e-4, plain and with the control variate of
+    v = u + 1e-2 sin(3 pi x) sin(2 pi y) on 129^2; nodes/s at RMSE 1e-3."""
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    ctx = pdd.Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_PAPER_EX_2D)
+    prob.set_control_grid(0, W.control_grid(W.PAPER_EX_2D, GRID_N, 1e-2))
+    nodes = W.workload_nodes("paper")
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).cuda() for j in range(2)]
+    u = W.exact_u(W.PAPER_EX_2D, nodes.astype(np.float64))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(smi_id(0))
+    modes, total_ms, total_steps = {}, 0.0, 0.0
+    for name, gid in (("plain", pdd.PDD_CV_NONE), ("cv_eps1e-2", 0)):
+        holder = {}
+
+        def step():
+            holder["r"] = prob.estimate(cols, N_PATHS, DT, grid_id=gid, async_=True)
+
+        for _ in range(args.warmup):
+            step()
+        ms = _timed_steps(torch, ctx.stream, args.steps, step, flush)
+        r = {k: v.cpu().numpy() for k, v in holder["r"].items() if torch.is_tensor(v)}
+        steps = float((r["mean_steps"] * r["n_paths"]).sum())
+        mean = r["mean_phi"] if gid == pdd.PDD_CV_NONE else r["mean_cv"]
+        var = r["var_phi"] if gid == pdd.PDD_CV_NONE else r["var_cv"]
+        rate = steps / (np.mean(ms) / 1e3)
+        # nodes/s at RMSE a: N_i = ceil(V_i / (a^2/2)) paths per node at the measured rate
+        need = np.ceil(var / (TARGET_RMSE**2 / 2.0)) * r["mean_steps"]
+        modes[name] = {"path_steps_per_s": rate, "ms": float(np.mean(ms)),
+                       "rmse_at_1e5_paths": float(np.sqrt(np.mean((mean - u) ** 2))),
+                       "median_var": float(np.median(var)),
+                       "nodes_per_s_at_rmse": len(nodes) / (float(need.sum()) / rate)}
+        total_ms += float(np.sum(ms))
+        total_steps += steps * len(ms)
+    clk = clocks.stop()
+    kappa = modes["plain"]["path_steps_per_s"] / modes["cv_eps1e-2"]["path_steps_per_s"]
+    sp = modes["cv_eps1e-2"]["nodes_per_s_at_rmse"] / modes["plain"]["nodes_per_s_at_rmse"]
+    prob.close()
+    ctx.close()
+    return {"workload": "paper", "metric": METRIC, "value": total_steps / (total_ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "paper's example PDE, assumed 4-strip domain, 18 nodes x 1e5 "
+                                   "paths, dt=1e-4, plain + control variate eps=1e-2 on 129^2",
+                       "l2": "flushed between steps (256 MB)"},
+            "modes": modes, "kappa": kappa, "cv_speedup_at_rmse": sp,
+            "target_rmse": TARGET_RMSE, "clocks": clk}
+
+
 def run_fit(args):
     """Algorithm 3 on the 24 nodes: cloud of 100 time steps in [1e-3, 1e-2],
     1,000 paths each, psi drawn alongside from w = sin(3 pi x) sin(2 pi y)."""
@@ -781,10 +840,29 @@ def run_fit(args):
     cloud = r["cloud"]
     work = float((cloud[:, :, 3] / cloud[:, :, 0]).sum() * 1000)  # E[tau_h]/h x paths
     u = W.exact_u(0, nodes.astype(np.float64))
+    # Algorithm 4 on the fitted constants: kappa from the per-step time of the
+    # control-variate and plain kernels on these nodes, starting tolerance 0.05
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).cuda() for j in range(2)]
+    rate = {}
+    for name, gid in (("plain", pdd.PDD_CV_NONE), ("cv", 0)):
+        prob.estimate(cols, 20000, 1e-3, grid_id=gid)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rr = prob.estimate(cols, 20000, 1e-3, grid_id=gid)
+        torch.cuda.synchronize()
+        rate[name] = float((rr["mean_steps"].cpu().numpy() * 20000).sum()) / (time.perf_counter() - t1)
+    kappa = rate["plain"] / rate["cv"]
+    t1 = time.perf_counter()
+    a_sched, sp_sched = pdd.pdd_schedule(r["K"], r["beta"], r["alpha"], r["V_phi"], r["V_psi"],
+                                         r["rho_phi_psi"], 1.0, kappa, 0.05)
+    sched_s = time.perf_counter() - t1
     out = {"workload": "fit", "metric": METRIC, "value": work / secs, "unit": UNIT,
            "seconds": secs, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "Algorithm 3, 24 nodes, 100 time steps in [1e-3, 1e-2], "
-                                  "1000 paths each, psi from a synthetic w grid"},
+                                  "1000 paths each, psi from a synthetic w grid; Algorithm 4 "
+                                  "from a0 = 0.05 on the fitted constants"},
+           "schedule": {"kappa": kappa, "tolerances": [float(x) for x in a_sched],
+                        "predicted_speedups": [float(x) for x in sp_sched], "seconds": sched_s},
            "E_phi_rmse_vs_exact": float(np.sqrt(np.mean((r["E_phi"] - u) ** 2))),
            "median_beta": float(np.median(r["beta"])), "median_V_phi": float(np.median(r["V_phi"])),
            "median_E_tau": float(np.median(r["E_tau"])), "median_K": float(np.median(r["K"])),
@@ -876,7 +954,7 @@ def main():
     if args.workload != "c1" and args.impl == "ours":
         if rank == 0:
             fn = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "c4": run_c4,
-                  "fit": run_fit, "mlmc": run_mlmc}[args.workload]
+                  "fit": run_fit, "mlmc": run_mlmc, "paper": run_paper}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":
