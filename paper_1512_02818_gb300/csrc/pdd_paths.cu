@@ -11,9 +11,13 @@
 // and every lane whose path has finished takes the next index of its warp's
 // batch at the next iteration boundary, so lanes stay busy whatever the
 // spread of exit times (paths of one node range over ~12x the mean number of
-// steps).  The grid is persistent (occupancy x
-// SM count blocks).  Per-node sums are exact integers, so which lane or warp
-// runs a path changes nothing in the results.
+// steps).  The grid is persistent (occupancy x SM count blocks).  A finished
+// path parks in its warp's exit ring in shared memory and is scored and
+// recorded later, 32 at a time by the whole warp; launches with at most 512
+// node records add into a per-block shared-memory copy of the records, which
+// the block adds into the global ones at the end.  Per-node sums are exact
+// integers, so which lane, warp or block runs a path changes nothing in the
+// results.
 //
 // One iteration takes as many Euler steps as one Philox block has normals
 // for: two steps in 2D (4 normals), four steps in 3D (3 blocks, 12 normals),
