@@ -98,16 +98,51 @@ def _oracle_task(task):
     return float(r["mean_steps"][0]) * n_paths
 
 
-def oracle_pool_time(tasks, cores):
+_GRADS = {}
+
+
+def _oracle_task_any(task):
+    """One node of the oracle for any workload (spawned worker):
+    task = (kind, eps, grid_n, node, n_paths, h, tag); eps None = plain."""
+    import numpy as np
+    import oracle
+    from paper_1512_02818_gb300 import workloads as W
+    kind, eps, gn, node, n_paths, h, tag = task
+    dim = 3 if kind == W.CUBE_3D else 2
+    grad, cv = None, oracle.CV_NONE
+    if eps is not None:
+        key = (kind, gn, eps)
+        if key not in _GRADS:
+            _GRADS[key] = oracle.build_gradient(dim, W.control_grid(kind, gn, eps))
+        grad = _GRADS[key]
+        cv = oracle.CV_GRID_CELLS16 if dim == 3 else oracle.CV_GRID
+    r = oracle.estimate_nodes(kind, np.asarray(node, dtype=np.float32)[None], n_paths, h,
+                              seed=SEED, tag=tag, cv=cv, grad=grad, grid_n=gn if grad is not None
+                              else 0, per_path=False)
+    return float(r["mean_steps"][0]) * n_paths
+
+
+def oracle_pool_time(tasks, cores, fn=_oracle_task):
     import oracle
     oracle.build()
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
-        pool.map(_oracle_task, tasks[:cores])  # warm the workers (imports, table builds)
+        pool.map(fn, tasks[:cores])  # warm the workers (imports, table builds)
         t0 = time.perf_counter()
-        steps = pool.map(_oracle_task, tasks)
+        steps = pool.map(fn, tasks)
         dt = time.perf_counter() - t0
     return sum(steps), dt
+
+
+def cpu_baseline_of(kind, eps, grid_n, nodes, n_paths, h, tag, sample):
+    """The oracle, as it stands, on all host cores over a bounded sample
+    (one task per node); returns the bench line's cpu_baseline object."""
+    cores = cpu_cores()
+    tasks = [(kind, eps, grid_n, tuple(float(c) for c in nd), n_paths, h, tag) for nd in nodes]
+    steps, secs = oracle_pool_time(tasks, cores, _oracle_task_any)
+    return {"value": steps / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample} ({steps:.3g} path-steps, {secs:.2f} s wall, FP64, one process "
+                      "per core)"}
 
 
 def cpu_cores():
@@ -453,6 +488,10 @@ def run_c2(args):
 
     from paper_1512_02818_gb300 import pdd
     from paper_1512_02818_gb300 import workloads as W
+    # oracle pool first: spawned workers, before this process touches the GPU
+    cpu = None if args.no_cpu_baseline else cpu_baseline_of(
+        W.CUBE_3D, 1e-3, 65, W.workload_nodes("c2")[::576], 1000, 1e-4, 3,
+        "level 3: 16 of the 9,216 nodes x 1e3 paths at h = 1e-4, eps = 1e-3 grid 65^3")
     dev = torch.device("cuda", 0)
     ctx = pdd.Context(0)
     torch.cuda.set_stream(ctx.stream)
@@ -511,7 +550,7 @@ def run_c2(args):
                        "l2": "flushed between steps (256 MB)"},
             "nodes_per_s": len(nodes) * args.steps / (total_ms / 1e3),
             "levels": per_level, "graph_captures": ctx.graph_count(),
-            "gpu_launches": int(launches), "clocks": clk,
+            "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
             "roofline": {"bound": "alu", "unit": "T thread-instr/s",
                          "achieved": 190.0 * value / 1e12,
                          "peak": torch.cuda.get_device_properties(0).multi_processor_count
@@ -655,6 +694,10 @@ def run_c4(args):
     import oracle
     from paper_1512_02818_gb300 import pdd
     from paper_1512_02818_gb300 import workloads as W
+    # oracle pool first: spawned workers, before this process touches the GPU
+    cpu = None if args.no_cpu_baseline else cpu_baseline_of(
+        W.ANISO_2D, 1e-2, 513, W.workload_nodes("c4")[::124][:256], 1000, 1e-4, 0,
+        "256 of the 31,744 nodes x 1e3 paths, eps = 1e-2 grid 513^2")
     dev = torch.device("cuda", 0)
     ctx = pdd.Context(0)
     torch.cuda.set_stream(ctx.stream)
@@ -720,7 +763,7 @@ def run_c4(args):
                                   "subdomains, 31744 nodes x 1e4 paths, dt=1e-4, eps=1e-2 grid "
                                   "513^2; precision study on 256 nodes"},
            "rmse_fp32_full": float(np.sqrt(np.mean((r["mean_cv"] - u) ** 2))),
-           "precision": prec, "clocks": clk}
+           "precision": prec, "clocks": clk, "cpu_baseline": cpu}
     p32.close()
     p64.close()
     ctx.close()
@@ -734,10 +777,13 @@ def run_c0(args):
 
     from paper_1512_02818_gb300 import pdd
     from paper_1512_02818_gb300 import workloads as W
+    nodes = W.workload_nodes("c0")
+    # oracle pool first: spawned workers, before this process touches the GPU
+    cpu = None if args.no_cpu_baseline else cpu_baseline_of(
+        W.CFG0_2D, None, 0, nodes, 10_000, 1e-3, 0, "the whole workload: 24 nodes x 1e4 paths")
     ctx = pdd.Context(0)
     torch.cuda.set_stream(ctx.stream)
     prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
-    nodes = W.workload_nodes("c0")
     cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).cuda() for j in range(2)]
     holder = {}
 
@@ -756,7 +802,8 @@ def run_c0(args):
            "config": {"workload": "2D CFG0, 2x2 subdomains, 24 nodes x 1e4 paths, dt=1e-3, plain"},
            "nodes_per_s": len(nodes) * len(ms) / (sum(ms) / 1e3),
            "rmse": float(np.sqrt(np.mean((r["mean_phi"] - u) ** 2))),
-           "max_err_over_se": float(np.max(np.abs(r["mean_phi"] - u) / r["se_phi"]))}
+           "max_err_over_se": float(np.max(np.abs(r["mean_phi"] - u) / r["se_phi"])),
+           "cpu_baseline": cpu}
     prob.close()
     ctx.close()
     return out
