@@ -69,7 +69,8 @@ def parse_args():
                     help="keep the library's default launch shape")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: 64 of the 256 nodes x 2e4 paths (same kernels)")
-    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit", "mlmc", "paper"],
+    ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit", "mlmc", "paper",
+                                           "peaks"],
                     default="c1",
                     help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c0: 24 nodes, "
                          "plain, dt 1e-3; fit: Algorithm 3 on the 24 nodes; c2: 3D "
@@ -867,6 +868,31 @@ def run_paper(args):
             "target_rmse": TARGET_RMSE, "clocks": clk}
 
 
+def run_peaks(args):
+    """Issue-rate probe: thread-operations/s of FP32 FMA, INT32 multiply-add,
+    SFU exp2 and 3-input logic ops, against the derived issue peak (one warp
+    instruction per scheduler per cycle at the maximum SM clock)."""
+    import torch
+
+    from paper_1512_02818_gb300 import pdd
+    torch.cuda.init()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 4 * 32 * 2.07e9
+    clocks = ClockSampler(smi_id(0))
+    rates = {}
+    for name, kind, iters in (("ffma", 0, 8192), ("imad", 1, 8192), ("sfu_ex2", 2, 2048),
+                              ("lop3", 3, 8192)):
+        ops, ms = pdd.pdd_debug_issue_rate(kind, iters)
+        rates[name] = {"thread_ops_per_s": ops, "ms": ms, "frac_of_issue_peak": ops / peak}
+    clk = clocks.stop()
+    return {"workload": "peaks", "metric": "thread-operations/s per instruction class",
+            "value": rates["ffma"]["thread_ops_per_s"], "unit": "thread-ops/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"issue-rate probe, {4 * sms} blocks x 512 threads, 8 "
+                                   "independent chains per thread"},
+            "issue_peak_derived": peak, "rates": rates, "clocks": clk}
+
+
 def run_fit(args):
     """Algorithm 3 on the 24 nodes: cloud of 100 time steps in [1e-3, 1e-2],
     1,000 paths each, psi drawn alongside from w = sin(3 pi x) sin(2 pi y)."""
@@ -1001,7 +1027,8 @@ def main():
     if args.workload != "c1" and args.impl == "ours":
         if rank == 0:
             fn = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "c4": run_c4,
-                  "fit": run_fit, "mlmc": run_mlmc, "paper": run_paper}[args.workload]
+                  "fit": run_fit, "mlmc": run_mlmc, "paper": run_paper,
+                  "peaks": run_peaks}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":

@@ -28,6 +28,16 @@ int pdd_debug_philox_curand(const uint32_t* ctr, const uint32_t* key, uint32_t* 
 int pdd_debug_normals(uint64_t seed, uint32_t tag, uint32_t node, uint32_t path, uint64_t first,
                       int64_t count, int precision, float* out_f32, double* out_f64);
 
+/* Issue-rate probe (no counterpart in the paper): thread-operations per second
+   of one instruction class, run by 4 x SM-count blocks of 512 threads on the
+   current device, each thread `iters` x 32 operations in 8 independent
+   chains.  kind 0: FP32 fused multiply-add, 1: 32-bit integer multiply-add,
+   2: SFU base-2 exponential, 3: 3-input logic operation.  It measures the
+   per-class issue limits that the path kernels' roofline assumes (one warp
+   instruction per scheduler per cycle).  Allocates and frees a sink of 4 B
+   per thread; synchronous.  iters in [1, 2^24].                            */
+int pdd_debug_issue_rate(int kind, int iters, double* ops_per_s, double* ms);
+
 #ifdef __cplusplus
 }
 #endif

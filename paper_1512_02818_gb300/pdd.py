@@ -195,6 +195,8 @@ _SIGS = [
     ("pdd_debug_normals", ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                          ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    ("pdd_debug_issue_rate", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double)]),
 ]
 
 
@@ -803,3 +805,11 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def pdd_debug_issue_rate(kind: int, iters: int) -> tuple[float, float]:
+    """Issue-rate probe of one instruction class on the current device:
+    returns (thread-operations per second, kernel milliseconds)."""
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pdd_debug_issue_rate(kind, iters, ctypes.byref(ops), ctypes.byref(ms)))
+    return ops.value, ms.value
