@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "pdd_device.cuh"
 #include "pdd_internal.h"
 
@@ -733,8 +735,8 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled(
 template <class P, class T, int CV, int D>
 static cudaError_t launch_coupled_one(const PathArgs& a, int num_sms, cudaStream_t st,
                                       int* blocks) {
-  static int per_sm[kMaxBlockThreads / 32 + 1] = {0};
-  static int attr = 0;
+  static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
+  static std::atomic<int> attr{0};
   return launch_persistent(paths_coupled<P, T, CV, D>, a, num_sms, st, blocks,
                            PairRing<T>::kBytes, &attr, per_sm);
 }
@@ -828,29 +830,30 @@ constexpr int kCacheBlockThreads = 512;  // default block size of cached launche
 // without the cache.
 template <class K>
 static cudaError_t launch_persistent(K kern, const PathArgs& a, int num_sms, cudaStream_t st,
-                                     int* blocks, size_t ring_per_warp, int* attr_set,
-                                     int* occ_cache) {
+                                     int* blocks, size_t ring_per_warp,
+                                     std::atomic<int>* attr_set, std::atomic<int>* occ_cache) {
   PathArgs b = a;
   const size_t cache = plan_cache(b);
   const int threads =
       a.block_threads > 0 ? a.block_threads : (cache > 0 ? kCacheBlockThreads : kBlockThreads);
   if (threads % 32 != 0 || threads > kMaxBlockThreads) return cudaErrorInvalidValue;
   const size_t smem = cache + (size_t)(threads / 32) * ring_per_warp;
-  if (smem > 48u * 1024u && (int)smem > *attr_set) {
+  if (smem > 48u * 1024u && (int)smem > attr_set->load(std::memory_order_relaxed)) {
     const int lim = (int)(cache_bytes(kCacheMaxNodes) + (kMaxBlockThreads / 32) * ring_per_warp);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
-    *attr_set = lim;
+    attr_set->store(lim, std::memory_order_relaxed);
   }
   int occ = 0;
-  if (cache == 0 && occ_cache[threads / 32] != 0) {
-    occ = occ_cache[threads / 32];
+  const int known = occ_cache[threads / 32].load(std::memory_order_relaxed);
+  if (cache == 0 && known != 0) {
+    occ = known;
   } else {
     int v = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem);
     if (e != cudaSuccess) return e;
     occ = v > 0 ? v : 1;
-    if (cache == 0) occ_cache[threads / 32] = occ;
+    if (cache == 0) occ_cache[threads / 32].store(occ, std::memory_order_relaxed);
   }
   const unsigned long long warps_needed = (a.total + 31ull) / 32ull;
   const unsigned long long blocks_needed =
@@ -871,8 +874,8 @@ static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, i
     kern = paths_3d<P, T, CV, MULTI>;
   else
     kern = paths_2d<P, T, CV, MULTI>;
-  static int per_sm[kMaxBlockThreads / 32 + 1] = {0};
-  static int attr = 0;
+  static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
+  static std::atomic<int> attr{0};
   return launch_persistent(kern, a, num_sms, st, blocks, ExitRing<T, P::kDim>::kBytes, &attr,
                            per_sm);
 }
