@@ -421,7 +421,8 @@ def run_ours(args, rank, world, local):
         "pass_rate_path_steps_per_s": rate,
         "clocks": clk,
         "timed_kernel_launches": n_timed,
-        "launch_shape": {"block_threads": tuned[0] or 128, "max_blocks": tuned[1],
+        "launch_shape": {"block_threads": tuned[0] or (512 if n_nodes <= 512 else 128),
+                         "max_blocks": tuned[1],
                          "chosen_by": "pdd_autotune on the eps=1e-2 pass" if tuned[2]
                          else "library default"},
     }
