@@ -175,3 +175,42 @@ def test_destroy_with_work_in_flight(env):
         srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"])
     srv.close()  # cancels and waits for the launches in flight; must return
     torch.cuda.synchronize()
+
+
+def test_concurrent_clients(env):
+    """Four client threads submit and poll at the same time (the binding
+    releases the interpreter lock in every C call); every result equals the
+    same request run alone."""
+    import threading
+    torch, pdd, ctx, prob = env
+    srv = pdd.Server(ctx, max_active=8, max_queue=64, quantum_path_steps=10_000_000)
+    per_client = [_requests(seed=100 + c, count=5) for c in range(4)]
+    for c, reqs in enumerate(per_client):
+        for i, r in enumerate(reqs):
+            r["stream_tag"] = 1000 + 10 * c + i
+    got, errors = {}, []
+
+    def client(c):
+        try:
+            tickets = [srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"],
+                                  seed=r["seed"], stream_tag=r["stream_tag"])
+                       for r in per_client[c]]
+            for i, (r, t) in enumerate(zip(per_client[c], tickets)):
+                st, res = _wait(srv, t, len(r["nodes"]))
+                got[(c, i)] = (st, res)
+        except Exception as ex:  # reported in the main thread
+            errors.append(repr(ex))
+
+    threads = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=300)
+    assert not errors, errors
+    assert len(got) == 20
+    srv.close()
+    for c, reqs in enumerate(per_client):
+        for i, r in enumerate(reqs):
+            st, res = got[(c, i)]
+            assert st == pdd.PDD_OK
+            _same(pdd, res, _alone(prob, r))
