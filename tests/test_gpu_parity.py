@@ -99,7 +99,7 @@ def test_paths_and_nodes_match_oracle(env, case):
     assert np.all(g["n_paths"].cpu().numpy() == case[3])
 
 
-@pytest.mark.parametrize("case", [CASES[2], CASES[7], CASES[1]], ids=["c1_grid", "cube_grid", "c0_exact"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_fp64_paths_match_oracle(env, case):
     g, ref = _run_case(env, case, precision=1)
     steps = g["steps"].cpu().numpy()
@@ -110,8 +110,8 @@ def test_fp64_paths_match_oracle(env, case):
     if not np.all(same):
         return
     for m in ("mean_phi", "mean_cv"):
-        rel = np.abs(g[m].cpu().numpy() - ref[m]) / np.abs(ref[m])
-        assert rel.max() < 1e-8, (m, rel.max())
+        d = np.abs(g[m].cpu().numpy() - ref[m])
+        assert np.all(d <= 1e-8 * np.abs(ref[m]) + 1e-12), (m, (d / np.abs(ref[m])).max())
     assert np.allclose(g["var_phi"].cpu().numpy(), ref["var_phi"], rtol=1e-7)
 
 
