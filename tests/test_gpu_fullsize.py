@@ -64,3 +64,93 @@ def test_c1_full_size_sampled_parity():
     assert np.all(full["n_truncated"].cpu().numpy() == 0)
     prob.close()
     ctx.close()
+
+
+def _sample_check(torch, full, ni, pi, ref, frac=0.995):
+    idx = (torch.from_numpy(ni), torch.from_numpy(pi))
+    phi = full["phi"][idx].cpu().numpy()
+    xi = full["xi"][idx].cpu().numpy()
+    steps = full["steps"][idx].cpu().numpy()
+    same = steps == ref["steps"]
+    ok = same & (np.abs(phi - ref["phi"]) <= PATH_ATOL) & (np.abs(xi - ref["xi"]) <= PATH_ATOL)
+    assert ok.mean() >= frac, (ok.mean(), (~same).sum())
+
+
+def test_c2_cascade_full_size_sampled_parity():
+    """The 3D cascade at full size (9,216 nodes; 1e3 / 1e4 / 1e5 paths at
+    dt 1e-2 / 1e-3 / 1e-4 on the eps 1e-1 / 1e-2 / 1e-3 grids, 65^3, plus the
+    plain level-1 pass) in one launch replayed from a CUDA graph, as the
+    benchmark runs it: the statistics equal those of the same launch with
+    per-path output, and sampled paths of every level match the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    from paper_1512_02818_gb300 import build, pdd
+    build.build()
+    oracle.build()
+    ctx = pdd.Context(0)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CUBE_3D)
+    cfg = W.WORKLOADS["c2"]["levels"]
+    grids = []
+    for slot, lv in enumerate(cfg):
+        v = W.control_grid(2, 65, lv["eps"])
+        prob.set_control_grid(slot, v)
+        grids.append(oracle.build_gradient(3, v))
+    nodes = W.workload_nodes("c2")
+    lv = [dict(nodes=nodes, n_paths=c["n_paths"], dt=c["dt"], grid_id=i, stream_tag=1 + i)
+          for i, c in enumerate(cfg)]
+    lv.append(dict(nodes=nodes, n_paths=cfg[0]["n_paths"], dt=cfg[0]["dt"],
+                   grid_id=pdd.PDD_CV_NONE, stream_tag=1))
+    st, bench = prob.estimate_levels(lv, graph=True)
+    assert st == 0
+    st, full = prob.estimate_levels([dict(l, emit_paths=True) for l in lv])
+    assert st == 0
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    for l, (a, b) in enumerate(zip(bench, full)):
+        for f in pdd.STAT_FIELDS + pdd.COUNT_FIELDS:
+            assert np.array_equal(a[f].cpu().numpy(), b[f].cpu().numpy(), equal_nan=True), (l, f)
+        m = 96
+        ni = rng.integers(0, nodes.shape[0], size=m)
+        pi = rng.integers(0, lv[l]["n_paths"], size=m)
+        gid = lv[l]["grid_id"]
+        ref = oracle.sample_paths(2, nodes, ni, pi, lv[l]["dt"], seed=1234, tag=lv[l]["stream_tag"],
+                                  cv=oracle.CV_NONE if gid < 0 else oracle.CV_GRID_CELLS16,
+                                  grad=None if gid < 0 else grids[gid], grid_n=0 if gid < 0 else 65)
+        _sample_check(torch, b, ni, pi, ref)
+    prob.close()
+    ctx.close()
+
+
+def test_c4_full_size_sampled_parity():
+    """The anisotropic 2D workload at full size (31,744 nodes x 1e4 paths, dt
+    1e-4, eps 1e-2 grid on 513^2): statistics equal to the launch without
+    per-path output, sampled paths match the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import oracle
+    from paper_1512_02818_gb300 import build, pdd
+    build.build()
+    oracle.build()
+    ctx = pdd.Context(0)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_ANISO_2D)
+    v = W.control_grid(1, 513, 1e-2)
+    prob.set_control_grid(0, v)
+    nodes = W.workload_nodes("c4")
+    N, h = 10_000, 1e-4
+    full = prob.estimate(nodes, N, h, grid_id=0, seed=1234, stream_tag=0, emit_paths=True)
+    bench = prob.estimate(nodes, N, h, grid_id=0, seed=1234, stream_tag=0, async_=True)
+    torch.cuda.synchronize()
+    for f in pdd.STAT_FIELDS + pdd.COUNT_FIELDS:
+        assert np.array_equal(full[f].cpu().numpy(), bench[f].cpu().numpy(), equal_nan=True), f
+    rng = np.random.default_rng(13)
+    m = 200
+    ni = rng.integers(0, nodes.shape[0], size=m)
+    pi = rng.integers(0, N, size=m)
+    ref = oracle.sample_paths(1, nodes, ni, pi, h, seed=1234, tag=0, cv=oracle.CV_GRID,
+                              grad=oracle.build_gradient(2, v), grid_n=513)
+    _sample_check(torch, full, ni, pi, ref)
+    prob.close()
+    ctx.close()
