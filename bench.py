@@ -557,7 +557,10 @@ def run_c2(args):
                          "achieved": 190.0 * value / 1e12,
                          "peak": torch.cuda.get_device_properties(0).multi_processor_count
                          * 4 * 32 * 2.070e9 / 1e12,
-                         "algorithmic": "190 thread-instr per 3D control-variate path-step"}}
+                         "algorithmic": "190 thread-instr per 3D control-variate path-step",
+                         "second_limit": "L1 data pipe: 79 % of its peak in the ncu capture of "
+                                         "the profiling case (two 256-bit cell-record gathers "
+                                         "per step), issue 74 %"}}
     line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     prob.close()
     ctx.close()
