@@ -583,9 +583,10 @@ def run_c3(args):
     prob.set_control_grid(1, W.control_grid(0, GRID_N, 1e-2))
     gid = {None: pdd.PDD_CV_NONE, 1e-1: 0, 1e-2: 1}
 
-    def serve(rate, window, drain_s, seed):
+    def serve(rate, window, drain_s, seed, policy=pdd.PDD_SERVE_FAIR):
         reqs = W.serving_requests(seed, rate, window)
-        srv = pdd.Server(ctx, max_active=32, max_queue=64, device_arena_bytes=1 << 30)
+        srv = pdd.Server(ctx, max_active=32, max_queue=64, device_arena_bytes=1 << 30,
+                         policy=policy)
         t0 = time.perf_counter()
         outstanding, lat, done_steps, done_nodes, rejected = {}, [], 0.0, 0, 0
         i = 0
@@ -667,6 +668,7 @@ def run_c3(args):
                        "rmse_vs_exact": float(np.sqrt(np.mean((mean - u) ** 2)))}
     fixed["cv_speedup_nodes_per_s"] = fixed["cv_eps1e-2"]["nodes_per_s"] / fixed["plain"]["nodes_per_s"]
     sat = serve(args.rate, args.window, 30.0, 11)
+    sat_short = serve(args.rate, args.window, 30.0, 11, pdd.PDD_SERVE_SHORTEST)
     # capacity in requests/s: sustained rate over the mean offered request size
     reqs = W.serving_requests(11, args.rate, args.window)
     mean_req = np.mean([r["n_nodes"] * r["n_paths"] * 0.12 / r["dt"] for r in reqs])
@@ -682,7 +684,8 @@ def run_c3(args):
                                    "1-4096 nodes, 1e3-1e6 paths (log-uniform), dt in "
                                    "{1e-2,1e-3,1e-4}, eps in {none,1e-1,1e-2}; max_active 32, "
                                    "max_queue 64, quantum 8e9 path-steps"},
-            "saturation": sat, "at_0.7x_capacity": steady,
+            "saturation": sat, "saturation_shortest_first": sat_short,
+            "at_0.7x_capacity": steady,
             "served_rate_one_request_path_steps_per_s": cal_rate,
             "fixed_rmse_served": {"target_rmse": a_t, **fixed},
             "mean_request_path_steps_est": float(mean_req),

@@ -418,10 +418,10 @@ int pdd_autotune(pdd_problem* problem, const pdd_estimate_args* sample, int* bes
    A server admits requests (one pdd_estimate_args each: nodes, n_paths, dt,
    grid, seed, stream_tag) while a slot of the running batch and room in its
    device arena are free, and runs the admitted requests together: every
-   scheduler iteration is one persistent launch that carries a slice of paths
-   from each of up to max_active requests (requests of the same problem and
-   control-variate class share a launch), so requests arriving while others
-   run join the next launch.  Results are bit-identical to pdd_estimate_nodes
+   scheduler iteration is one persistent launch that carries slices of paths
+   of up to max_active requests (requests of the same problem and
+   control-variate class share a launch; `policy` decides the slices), so
+   requests arriving while others run join the next launch.  Results are bit-identical to pdd_estimate_nodes
    on the same arguments (exact sums keyed by node and path).  A scheduler
    thread owned by the server issues launches on two streams of its own and
    polls CUDA events; nothing on the device waits.                          */
@@ -431,7 +431,15 @@ typedef struct {
   int64_t quantum_path_steps;  /* target path-steps per launch (0: 8e9) */
   size_t device_arena_bytes;   /* device memory for admitted requests (0: 256 MiB);
                                   a request takes about 252 B per node */
+  int32_t policy;              /* how a launch's path-steps are shared among the batch:
+                                  PDD_SERVE_FAIR (0): equal shares; PDD_SERVE_SHORTEST (1):
+                                  requests with the least remaining work first, each up to
+                                  all its remaining paths, until the quantum is spent (less
+                                  latency for small requests; large ones wait under overload) */
+  int32_t reserved;            /* 0 */
 } pdd_server_desc;
+#define PDD_SERVE_FAIR 0
+#define PDD_SERVE_SHORTEST 1
 
 typedef struct {
   int64_t submitted, admitted, rejected_busy, rejected_invalid, rejected_nomem;

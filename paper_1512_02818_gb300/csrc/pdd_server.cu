@@ -3,9 +3,11 @@
 // A request (nodes, n_paths, dt, control grid, seed, tag) is admitted when a
 // slot of the running batch and room in the device arena are free.  Every
 // scheduler iteration issues ONE multi-segment launch of the path kernel that
-// carries a slice of paths (path indices p0 .. p0+m-1 of every node) from each
-// admitted request, so requests that arrive while others run join the next
-// launch, and long requests progress while short ones come and go.  Launches
+// carries slices of paths (path indices p0 .. p0+m-1 of every node) of the
+// admitted requests -- equal shares of the launch's path-steps, or (policy
+// PDD_SERVE_SHORTEST) the requests with the least remaining work first -- so
+// requests that arrive while others run join the next launch, and long
+// requests progress while short ones come and go.  Launches
 // alternate between two streams, so the next launch's blocks fill SMs while
 // the previous launch drains.  A request's node records accumulate exact
 // integer sums across its slices, so its result is bit-identical to running
@@ -259,6 +261,41 @@ bool issue_launch(pdd_server* s) {
       batch.push_back(&r);
     if ((int)batch.size() == kMaxSegments) break;
   }
+  // paths of every request in this launch: equal shares of the quantum, or
+  // the least remaining work first, each request up to all its paths
+  auto per_path_of = [](const Request* r) {
+    return std::max(1.0, r->est_steps) * (double)r->n_nodes;
+  };
+  const double quantum = (double)s->desc.quantum_path_steps;
+  std::vector<uint64_t> take(batch.size(), 0);
+  if (s->desc.policy == PDD_SERVE_SHORTEST) {
+    std::stable_sort(batch.begin(), batch.end(), [&](const Request* x, const Request* y) {
+      return (double)(x->n_paths - x->next_path) * per_path_of(x) <
+             (double)(y->n_paths - y->next_path) * per_path_of(y);
+    });
+    double budget = quantum;
+    for (size_t i = 0; i < batch.size() && budget > 0.0; ++i) {
+      const double pp = per_path_of(batch[i]);
+      const uint64_t m = (uint64_t)std::max(1.0, std::floor(budget / pp));
+      take[i] = std::min<uint64_t>(m, batch[i]->n_paths - batch[i]->next_path);
+      budget -= (double)take[i] * pp;
+    }
+  } else {
+    const double share = quantum / (double)batch.size();
+    for (size_t i = 0; i < batch.size(); ++i) {
+      const uint64_t m = (uint64_t)std::max(1.0, std::floor(share / per_path_of(batch[i])));
+      take[i] = std::min<uint64_t>(m, batch[i]->n_paths - batch[i]->next_path);
+    }
+  }
+  size_t kept = 0;
+  for (size_t i = 0; i < batch.size(); ++i)
+    if (take[i] > 0) {
+      batch[kept] = batch[i];
+      take[kept] = take[i];
+      ++kept;
+    }
+  batch.resize(kept);
+  take.resize(kept);
   const ProblemView& pv = batch[0]->pv;
   int cv = 0;
   for (Request* r : batch) cv = std::max(cv, r->cv);
@@ -279,15 +316,13 @@ bool issue_launch(pdd_server* s) {
   ctx_view(s->ctx, &dev, &sms, &bt, &mb);
   pa.block_threads = bt;
   pa.max_blocks = mb;
-  const double share = (double)s->desc.quantum_path_steps / (double)batch.size();
   unsigned long long begin = 0;
   int ns = 0;
   Launch L;
-  for (Request* r : batch) {
+  for (size_t bi = 0; bi < batch.size(); ++bi) {
+    Request* r = batch[bi];
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, r->ready, 0);
-    const double per_path = std::max(1.0, r->est_steps) * (double)r->n_nodes;
-    uint64_t m = (uint64_t)std::max(1.0, std::floor(share / per_path));
-    m = std::min<uint64_t>(m, r->n_paths - r->next_path);
+    const uint64_t m = take[bi];
     SegArgs& sg = pa.seg[ns++];
     sg.cx = req_coord(s, *r, 0);
     sg.cy = req_coord(s, *r, 1);
@@ -447,6 +482,10 @@ int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** ou
   if (d.max_queue <= 0) d.max_queue = 256;
   if (d.quantum_path_steps <= 0) d.quantum_path_steps = 8000000000ll;
   if (d.device_arena_bytes == 0) d.device_arena_bytes = (size_t)256 << 20;
+  if (d.policy != PDD_SERVE_FAIR && d.policy != PDD_SERVE_SHORTEST) {
+    set_error("pdd_server_create: policy %d is not PDD_SERVE_FAIR or PDD_SERVE_SHORTEST", d.policy);
+    return PDD_ERR_INVALID;
+  }
   auto s = std::make_unique<pdd_server>();
   s->ctx = ctx;
   s->desc = d;

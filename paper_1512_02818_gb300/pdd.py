@@ -95,7 +95,11 @@ class ScheduleArgs(ctypes.Structure):
 
 class ServerDesc(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("max_queue", ctypes.c_int32),
-                ("quantum_path_steps", ctypes.c_int64), ("device_arena_bytes", ctypes.c_size_t)]
+                ("quantum_path_steps", ctypes.c_int64), ("device_arena_bytes", ctypes.c_size_t),
+                ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+PDD_SERVE_FAIR, PDD_SERVE_SHORTEST = 0, 1
 
 
 class MlmcArgs(ctypes.Structure):
@@ -746,11 +750,12 @@ class Server:
     """Continuous-batching server on a context (see pdd_server_create)."""
 
     def __init__(self, ctx: Context, max_active: int = 0, max_queue: int = 0,
-                 quantum_path_steps: int = 0, device_arena_bytes: int = 0):
+                 quantum_path_steps: int = 0, device_arena_bytes: int = 0,
+                 policy: int = PDD_SERVE_FAIR):
         self.ctx = ctx
         self.handle = pdd_server_create(ctx.handle, ServerDesc(max_active, max_queue,
                                                                quantum_path_steps,
-                                                               device_arena_bytes))
+                                                               device_arena_bytes, policy, 0))
 
     def submit(self, problem: Problem, nodes, n_paths: int, dt: float,
                grid_id: int = PDD_CV_NONE, seed: int = 1234, stream_tag: int = 0,

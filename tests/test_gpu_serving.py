@@ -214,3 +214,31 @@ def test_concurrent_clients(env):
             st, res = got[(c, i)]
             assert st == pdd.PDD_OK
             _same(pdd, res, _alone(prob, r))
+
+
+def test_shortest_first_policy(env):
+    """PDD_SERVE_SHORTEST gives the launches to the requests with the least
+    remaining work: small requests submitted after a large one finish while it
+    is still running; every result still equals the request run alone."""
+    torch, pdd, ctx, prob = env
+    srv = pdd.Server(ctx, max_active=8, quantum_path_steps=500_000_000,
+                     policy=pdd.PDD_SERVE_SHORTEST)
+    big = dict(nodes=W.workload_nodes("c1"), n_paths=200_000, dt=1e-4, grid_id=1,
+               stream_tag=70, seed=3)
+    tb = srv.submit(prob, big["nodes"], big["n_paths"], big["dt"], grid_id=1, seed=3,
+                    stream_tag=70)
+    small = _requests(seed=51, count=6)
+    ts = [srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"],
+                     seed=r["seed"], stream_tag=r["stream_tag"]) for r in small]
+    for r, t in zip(small, ts):
+        st, res = _wait(srv, t, len(r["nodes"]))
+        assert st == pdd.PDD_OK
+        _same(pdd, res, _alone(prob, r))
+    st, _ = srv.poll(tb, len(big["nodes"]), 0)
+    assert st == pdd.PDD_ERR_NOT_READY  # the large request is still running
+    st, res = _wait(srv, tb, len(big["nodes"]))
+    assert st == pdd.PDD_OK
+    _same(pdd, res, _alone(prob, big))
+    srv.close()
+    with pytest.raises(pdd.PddError):
+        pdd.Server(ctx, policy=7)
