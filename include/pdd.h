@@ -493,6 +493,13 @@ void pdd_server_destroy(pdd_server* server);
    - The first call on each device looks up and caches the array's device
      address (cudaGetSymbolAddress); make that first call before any stream
      capture.
+   - With CUDA's lazy module loading (the default), the first launch of each
+     kernel variant -- one per (problem kind, path precision, control-variate
+     mode: none, grid or exact) -- loads that kernel, and loading can reserve
+     device memory.  Warm up once per variant (any call, e.g. with few paths)
+     before relying on the call allocating nothing.
+   - The launch shape is the context's (pdd_ctx_set_launch / pdd_autotune), as
+     for pdd_estimate_nodes; the caller's current device is left unchanged.
    - Every call uses the same array, which keeps the previous call's contents
      (each call clears what must start at zero).  Calls that can overlap on
      the GPU -- different streams or different contexts -- race on it and give

@@ -30,25 +30,6 @@ void set_error(const char* fmt, ...) {
   g_last_error = buf;
 }
 
-// Makes `dev` current for the lifetime of the guard.  cudaSetDevice is called
-// even when `dev` is already the current device: it (re)binds the device's
-// primary context to the calling thread, which other libraries in the process
-// may have changed.  A stale error left by an unchecked earlier call is
-// cleared so that it cannot be reported against this call.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    ok = cudaSetDevice(dev) == cudaSuccess;
-    (void)cudaGetLastError();
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 static int cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: CUDA error %d (%s)", what, (int)e, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? PDD_ERR_NOMEM : PDD_ERR_CUDA;

@@ -97,7 +97,8 @@ extern "C" int pdd_fit_constants(pdd_problem* p, const pdd_fit_args* a, pdd_fit_
   const size_t n = (size_t)a->n_nodes, M = (size_t)a->n_h;
   // per (h, field, node) device statistics: mean_phi, var_phi, mean_steps, cov, var_xi
   const int kF = 5;
-  if (cudaSetDevice(pv.device) != cudaSuccess) {
+  DeviceGuard guard(pv.device);  // restores the caller's device on return
+  if (!guard.ok) {
     set_error("pdd_fit_constants: cannot select device %d", pv.device);
     return PDD_ERR_CUDA;
   }

@@ -83,6 +83,25 @@ struct StatPtrs {
   unsigned long long* n_truncated;
 };
 
+// Makes `dev` current for the lifetime of the guard.  cudaSetDevice is called
+// even when `dev` is already the current device: it (re)binds the device's
+// primary context to the calling thread, which other libraries in the process
+// may have changed.  A stale error left by an unchecked earlier call is
+// cleared so that it cannot be reported against this call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+    (void)cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
 // What the allocation-free entry point needs to know about a problem.
 struct ProblemView {
   int device;

@@ -134,11 +134,16 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   if (max_steps > 2000000000ll) max_steps = 2000000000ll;
 
   std::lock_guard<std::mutex> lk(*pv.mu);
-  if (cudaSetDevice(pv.device) != cudaSuccess) {
+  // the caller's current device is restored on every return
+  DeviceGuard guard(pv.device);
+  if (!guard.ok) {
     set_error("pdd_estimate_nodes_noalloc: cannot select device %d", pv.device);
     return PDD_ERR_CUDA;
   }
-  (void)cudaGetLastError();
+  // the launch shape of the context (pdd_ctx_set_launch / pdd_autotune), as
+  // pdd_estimate_nodes uses it
+  int ctx_dev = 0, ctx_sms = 0, block_threads = 0, max_blocks = 0;
+  ctx_view(problem_ctx(problem), &ctx_dev, &ctx_sms, &block_threads, &max_blocks);
   void* scratch = nullptr;
   int rc = scratch_address(pv.device, &scratch);
   if (rc != PDD_OK) return rc;
@@ -157,8 +162,8 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   pa.err = &hdr->err;
   pa.trunc_total = &hdr->trunc_total;
   pa.y_exp = pv.y_rule == PDD_Y_EXP;
-  pa.max_blocks = 0;
-  pa.block_threads = 0;
+  pa.max_blocks = max_blocks;
+  pa.block_threads = block_threads;
   pa.n_segs = 1;
   SegArgs& sg = pa.seg[0];
   sg.cx = a->coords[0];

@@ -491,11 +491,11 @@ int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** ou
   s->desc = d;
   int bt = 0, mb = 0;
   ctx_view(ctx, &s->device, &s->num_sms, &bt, &mb);
-  if (cudaSetDevice(s->device) != cudaSuccess) {
+  DeviceGuard guard(s->device);  // restores the caller's device on return
+  if (!guard.ok) {
     set_error("pdd_server_create: cannot select device %d", s->device);
     return PDD_ERR_CUDA;
   }
-  (void)cudaGetLastError();
   // host results need 112 of every 252 device bytes per node
   const size_t host_bytes = d.device_arena_bytes / 2 + (1 << 20);
   cudaError_t e = cudaMalloc((void**)&s->dev_arena, d.device_arena_bytes);
@@ -585,7 +585,7 @@ int pdd_submit(pdd_server* s, pdd_problem* p, const pdd_estimate_args* a, uint64
     r->coords[j].resize((size_t)a->n_nodes);
     if (a->n_nodes == 0) continue;
     if (a->coords_on_device) {
-      cudaSetDevice(s->device);
+      DeviceGuard guard(s->device);
       cudaError_t e = cudaMemcpy(r->coords[j].data(), a->coords[j], (size_t)a->n_nodes * 4,
                                  cudaMemcpyDeviceToHost);
       if (e != cudaSuccess) {
@@ -739,7 +739,7 @@ void pdd_server_destroy(pdd_server* s) {
     s->cv_work.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
-  cudaSetDevice(s->device);
+  DeviceGuard guard(s->device);
   for (auto& x : s->stream) cudaStreamSynchronize(x);
   cudaStreamSynchronize(s->copy_stream);
   for (auto& kv : s->reqs) {

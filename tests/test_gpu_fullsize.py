@@ -81,7 +81,9 @@ def test_c2_cascade_full_size_sampled_parity():
     dt 1e-2 / 1e-3 / 1e-4 on the eps 1e-1 / 1e-2 / 1e-3 grids, 65^3, plus the
     plain level-1 pass) in one launch replayed from a CUDA graph, as the
     benchmark runs it: the statistics equal those of the same launch with
-    per-path output, and sampled paths of every level match the oracle."""
+    per-path output, and sampled paths of every level match the oracle's
+    plain trilinear interpolation of the nodal gradient table (the FP32 3D
+    kernel itself reads the binary16 cell table)."""
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
@@ -116,7 +118,7 @@ def test_c2_cascade_full_size_sampled_parity():
         pi = rng.integers(0, lv[l]["n_paths"], size=m)
         gid = lv[l]["grid_id"]
         ref = oracle.sample_paths(2, nodes, ni, pi, lv[l]["dt"], seed=1234, tag=lv[l]["stream_tag"],
-                                  cv=oracle.CV_NONE if gid < 0 else oracle.CV_GRID_CELLS16,
+                                  cv=oracle.CV_NONE if gid < 0 else oracle.CV_GRID,
                                   grad=None if gid < 0 else grids[gid], grid_n=0 if gid < 0 else 65)
         _sample_check(torch, b, ni, pi, ref)
     prob.close()
