@@ -43,14 +43,17 @@ GRID_N = 129
 EPS = [1e-1, 1e-2, 1e-3]
 SEED = 1234
 TARGET_RMSE = 1e-3
-# Algorithmic thread-instructions per path-step (planning count of the
-# per-step work: Philox share, Box-Muller, coefficients, updates, exit test,
-# and for the control variate the bilinear gradient and xi update).
-ALGO_INSTR = {"plain": 110.0, "cv": 150.0}
-# DRAM bytes (read + write) per launch of the dominant kernel from the ncu
-# capture summarised in profiles/paths_2d_cv_profiling_case.md; None whenever
-# the kernel has changed since that capture.
-NCU_TRAFFIC_BYTES = 909824
+# Thread-instructions per path-step of the 2D kernels (Philox share,
+# Box-Muller, coefficients, updates, exit test, and for the control variate
+# the cell record, bilinear gradient and xi update), as executed: ncu's
+# smsp__thread_inst_executed.sum over the path-steps of the full-size launches
+# (profiles/paths_2d_c1_256nodes_1e5paths_counters.md; the planning estimates
+# were 110 and 150).
+ALGO_INSTR = {"plain": 111.2, "cv": 140.1}
+# DRAM bytes (read + write) per launch of the dominant kernel (the eps = 1e-2
+# pass) from the same full-size capture; None whenever the kernel has changed
+# since that capture.
+NCU_TRAFFIC_BYTES = 1461248
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
@@ -68,9 +71,10 @@ def parse_args():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shape")
     ap.add_argument("--small", action="store_true",
-                    help="profiling case: 64 of the 256 nodes x 2e4 paths (same kernels)")
+                    help="profiling case: the 256 nodes x 1e4 paths (same kernels, launch "
+                         "shape and passes as the default step)")
     ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit", "mlmc", "paper",
-                                           "peaks"],
+                                           "peaks", "cascade"],
                     default="c1",
                     help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c0: 24 nodes, "
                          "plain, dt 1e-3; fit: Algorithm 3 on the 24 nodes; c2: 3D "
@@ -78,8 +82,11 @@ def parse_args():
                          "Poisson arrivals; c4: anisotropic 2D, FP32 vs FP64 paths; mlmc: "
                          "multilevel driver at a fixed RMSE vs the single level; paper: the "
                          "paper's example PDE on 18 nodes")
+    ap.add_argument("--a0", type=float, default=1e-3, help="cascade: nodal target tolerance")
     ap.add_argument("--window", type=float, default=10.0, help="c3: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="c3: arrivals per second")
+    ap.add_argument("--deadline", type=float, default=10.0,
+                    help="c3: admission deadline (s) of the server at the offered rate")
     return ap.parse_args()
 
 
@@ -254,6 +261,71 @@ def stream_tag(rank: int, pass_idx: int) -> int:
 
 
 # ---------------------------------------------------------------- our arm -----
+def fixed_rmse_runs(torch, pdd, prob, dev, nodes_np, res_np, passes, rank, target):
+    """Measured nodes/s at a fixed RMSE `target` for every mode of the step.
+
+    For node i and mode m, N_i = ceil(V_i / (target^2 / 2)) paths, V_i being
+    the mode's per-node variance from the timed step (plain: V[phi], control
+    variate: V[phi + xi]), so that the statistical error of every node is at
+    most target / sqrt(2) (the balanced choice of eq. F:N_y_h; the rest of the
+    budget is the bias).  The nodes are sorted by N_i and split into up to 128
+    groups, each run as one level of a single pdd_estimate_levels call with
+    the group's largest N_i and a stream of its own.  The call (device-resident
+    inputs and outputs, synchronous) is timed on the host clock, after a
+    1-path-per-node call of the same levels loaded the kernel.  The achieved
+    RMSE is against the exact solution over all nodes, bias included."""
+    import numpy as np
+    from paper_1512_02818_gb300 import workloads as W
+    n = nodes_np.shape[0]
+    u = W.exact_u(0, nodes_np.astype(np.float64))
+    out = {"target_rmse": target, "measured": True}
+    for pi, (name, gid) in enumerate(passes):
+        r = res_np[pi]
+        var = r["var_phi"] if gid == pdd.PDD_CV_NONE else r["var_cv"]
+        need = np.maximum(2, np.ceil(var / (target * target / 2.0))).astype(np.int64)
+        groups = [g for g in np.array_split(np.argsort(need, kind="stable"), min(128, n))
+                  if g.size]
+        levels = []
+        for gi, idx in enumerate(groups):
+            cols = [torch.from_numpy(np.ascontiguousarray(nodes_np[idx, j])).to(dev)
+                    for j in range(2)]
+            levels.append((idx, cols, int(need[idx].max()),
+                           1_000_000 + 4096 * rank + 512 * pi + gi))
+
+        def prep(n_paths_of):
+            pr = [prob._prepare(cols, n_paths_of(np_), DT, gid, SEED, tag, 1.0, False, True,
+                                False, False) for (_, cols, np_, tag) in levels]
+            return [p[0] for p in pr], [p[1] for p in pr], [p[2] for p in pr]
+
+        wa, wo, _ = prep(lambda _: 1)
+        st = pdd.pdd_estimate_levels(prob.handle, wa, wo, 0)
+        la, lo, lres = prep(lambda np_: np_)
+        torch.cuda.synchronize()
+        prob.ctx.set_timing(True)
+        prob.ctx.kernel_time()
+        t0 = time.perf_counter()
+        st = pdd.pdd_estimate_levels(prob.handle, la, lo, 0)
+        wall = time.perf_counter() - t0
+        kernel_ms, _, _ = prob.ctx.kernel_time()
+        prob.ctx.set_timing(False)
+        est = np.zeros(n)
+        path_steps = 0.0
+        key = "mean_phi" if gid == pdd.PDD_CV_NONE else "mean_cv"
+        for (idx, _, np_, _), rr in zip(levels, lres):
+            est[idx] = rr[key].cpu().numpy()
+            path_steps += float((rr["mean_steps"].cpu().numpy() * np_).sum())
+        out[name] = {"nodes_per_s": n / wall, "wall_s": wall, "status": int(st),
+                     "path_kernel_s": kernel_ms / 1e3, "segments": len(levels),
+                     "paths": int(sum(np_ * len(idx) for (idx, _, np_, _) in levels)),
+                     "path_steps": path_steps, "path_steps_per_s": path_steps / wall,
+                     "achieved_rmse": float(np.sqrt(np.mean((est - u) ** 2))),
+                     "median_paths_per_node": float(np.median(need)),
+                     "median_var": float(np.median(var))}
+    for name, _ in passes[1:]:
+        out[name]["speedup_vs_plain"] = out[name]["nodes_per_s"] / out["plain"]["nodes_per_s"]
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -288,7 +360,7 @@ def run_ours(args, rank, world, local):
     nodes_np = W.workload_nodes("c1")
     n_paths = N_PATHS
     if args.small:
-        nodes_np, n_paths = nodes_np[::4].copy(), 20_000
+        n_paths = 10_000
     n_nodes = nodes_np.shape[0]
     cols_dev = [torch.from_numpy(np.ascontiguousarray(nodes_np[:, j])).to(dev) for j in range(2)]
     cols_host = [torch.from_numpy(np.ascontiguousarray(nodes_np[:, j])).pin_memory()
@@ -358,30 +430,26 @@ def run_ours(args, rank, world, local):
     instr = ALGO_INSTR["cv"] * pass_steps[2]
     achieved = instr / (avg_ms / 1e3) / 1e12
     peak = sms * 4 * 32 * 2.070e9 / 1e12  # one warp instruction per SMSP per cycle at max clock
+    plain_ms = statistics.mean(dur["plain"])
+    plain_frac = ALGO_INSTR["plain"] * pass_steps[0] / (plain_ms / 1e3) / 1e12 / peak
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "T thread-instr/s", "frac": achieved / peak, "traffic": NCU_TRAFFIC_BYTES,
                 "kernel": "paths_2d<Cfg0,float,grid-CV>",
-                "algorithmic": f"{ALGO_INSTR['cv']:.0f} thread-instr per path-step x "
-                               f"{pass_steps[2]:.4g} path-steps per launch",
-                "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x 2070 MHz"}
+                "algorithmic": f"{ALGO_INSTR['cv']:.1f} thread-instr per path-step (ncu, "
+                               f"executed) x {pass_steps[2]:.4g} path-steps per launch",
+                "peak_basis": f"{sms} SMs x 4 schedulers x 32 lanes x 2070 MHz "
+                              "(derived issue peak)",
+                "plain_kernel_frac": plain_frac}
 
-    # nodes/s at a fixed RMSE (balanced choice of N per node, Sec. 3.1)
-    u = W.exact_u(0, nodes_np.astype(np.float64))
-    fixed = {}
-    for i, (name, _) in enumerate(passes):
-        r = res_np[i]
-        var = r["var_phi"] if name == "plain" else r["var_cv"]
-        mean = r["mean_phi"] if name == "plain" else r["mean_cv"]
-        need = np.ceil(var / (TARGET_RMSE**2 / 2.0))
-        secs = float((need * r["mean_steps"]).sum()) / rate[name]
-        fixed[name] = {"nodes_per_s": n_nodes / secs,
-                       "rmse_at_1e5_paths": float(np.sqrt(np.mean((mean - u) ** 2))),
-                       "median_var": float(np.median(var))}
+    # nodes/s at a fixed RMSE, measured: per node N_i = ceil(V_i / (a^2/2))
+    # paths (the balanced choice of eq. F:N_y_h) with V_i from the timed step,
+    # then every mode run at those N through the library and timed
+    fixed = fixed_rmse_runs(torch, pdd, prob, dev, nodes_np, res_np, passes, rank,
+                            TARGET_RMSE if not args.small else 4 * TARGET_RMSE)
     for i, (name, _) in enumerate(passes):
         if i == 0:
             continue
         r = res_np[i]
-        fixed[name]["speedup_vs_plain"] = fixed[name]["nodes_per_s"] / fixed["plain"]["nodes_per_s"]
         pred = r["var_phi"] / (kappa[name] * r["var_cv"])
         fixed[name]["predicted_speedup_median"] = float(np.median(pred))
         fixed[name]["kappa"] = kappa[name]
@@ -417,7 +485,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "cpu_baseline": cpu_baseline,
-        "fixed_rmse": {"target_rmse": TARGET_RMSE, **fixed},
+        "fixed_rmse": fixed,
         "pass_rate_path_steps_per_s": rate,
         "clocks": clk,
         "timed_kernel_launches": n_timed,
@@ -570,8 +638,11 @@ def run_c2(args):
 def run_c3(args):
     """Serving: Poisson arrivals of requests over the 2D problem (1-4,096 nodes
     log-uniform, 1e3-1e6 paths log-uniform, dt in {1e-2,1e-3,1e-4}, eps in
-    {none, 1e-1, 1e-2}); continuous batching; p50/p99 latency of completed
-    requests.  Runs the offered rate, then 0.7x the measured capacity."""
+    {none, 1e-1, 1e-2}); continuous batching with admission by predicted work
+    against a deadline; p50/p99 latency of completed requests and goodput
+    (completed over executed path-steps).  Runs the offered rate, then an
+    arrival rate whose offered path-steps/s are 0.7x the served rate of one
+    large request."""
     import numpy as np
     import torch
 
@@ -583,12 +654,14 @@ def run_c3(args):
     prob.set_control_grid(1, W.control_grid(0, GRID_N, 1e-2))
     gid = {None: pdd.PDD_CV_NONE, 1e-1: 0, 1e-2: 1}
 
-    def serve(rate, window, drain_s, seed, policy=pdd.PDD_SERVE_FAIR):
+    def serve(rate, window, drain_s, seed, policy=pdd.PDD_SERVE_FAIR, deadline=0.0,
+              steps_of=None):
         reqs = W.serving_requests(seed, rate, window)
         srv = pdd.Server(ctx, max_active=32, max_queue=64, device_arena_bytes=1 << 30,
-                         policy=policy)
+                         policy=policy, deadline_s=deadline)
         t0 = time.perf_counter()
-        outstanding, lat, done_steps, done_nodes, rejected = {}, [], 0.0, 0, 0
+        outstanding, lat, done_steps, done_nodes = {}, [], 0.0, 0
+        refused = {"busy": 0, "deadline": 0, "nomem": 0, "other": 0}
         i = 0
 
         def poll_all():
@@ -604,6 +677,8 @@ def run_c3(args):
                     done_steps += float((res["mean_steps"] * res["n_paths"]).sum())
                     done_nodes += r["n_nodes"]
 
+        names = {pdd.PDD_ERR_BUSY: "busy", pdd.PDD_ERR_DEADLINE: "deadline",
+                 pdd.PDD_ERR_NOMEM: "nomem"}
         while i < len(reqs) or (outstanding and time.perf_counter() - t0 < window + drain_s):
             now = time.perf_counter() - t0
             while i < len(reqs) and reqs[i]["arrival"] <= now:
@@ -613,8 +688,8 @@ def run_c3(args):
                     t = srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=gid[r["eps"]],
                                    seed=SEED, stream_tag=r["tag"])
                     outstanding[t] = r
-                except pdd.PddError:
-                    rejected += 1
+                except pdd.PddError as e:
+                    refused[names.get(e.status, "other")] += 1
             poll_all()
             time.sleep(0.001)
         elapsed = time.perf_counter() - t0
@@ -623,10 +698,12 @@ def run_c3(args):
             srv.cancel(t)
         stats = srv.stats()
         srv.close()
-        offered = sum(float(r["n_nodes"]) * r["n_paths"] * 0.12 / r["dt"] for r in reqs)
-        return {"rate_per_s": rate, "window_s": window, "offered_requests": len(reqs),
-                "offered_path_steps_per_s_est": offered / window,
-                "completed": len(lat), "rejected_busy": rejected,
+        offered = sum(float(r["n_nodes"]) * r["n_paths"] * steps_of(r["dt"]) for r in reqs)
+        return {"rate_per_s": rate, "window_s": window, "deadline_s": deadline,
+                "policy": {pdd.PDD_SERVE_SHORTEST: "shortest_first", pdd.PDD_SERVE_FAIR: "fair",
+                           pdd.PDD_SERVE_EARLIEST_DEADLINE: "earliest_deadline"}[policy],
+                "offered_requests": len(reqs), "offered_path_steps_per_s": offered / window,
+                "completed": len(lat), "refused": refused,
                 "cancelled_at_end": unfinished, "launches": stats["launches"],
                 "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat else None,
                 "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat else None,
@@ -634,7 +711,10 @@ def run_c3(args):
                 "completed_nodes_per_s": done_nodes / elapsed, "elapsed_s": elapsed,
                 # every path-step the retired launches ran, including the slices of
                 # requests still running (or cancelled) when the window closed
-                "executed_path_steps_per_s": stats["path_steps"] / elapsed}
+                "executed_path_steps_per_s": stats["path_steps"] / elapsed,
+                "goodput": (stats["completed_path_steps"] / stats["path_steps"]
+                            if stats["path_steps"] else None),
+                "server_rate_estimate": stats["rate_path_steps_per_s"]}
 
     clocks = ClockSampler(smi_id(0))
     # capacity: one large request (256 nodes x 1e5 paths, dt 1e-4, eps 1e-2) alone
@@ -647,6 +727,12 @@ def run_c3(args):
     cal_s = time.perf_counter() - tc
     srv.close()
     cal_rate = float((res["mean_steps"] * res["n_paths"]).sum()) / cal_s
+    # expected exit time on the interfaces (tau = k dt), for the offered work
+    e_tau = float(np.mean(res["mean_steps"])) * DT
+
+    def steps_of(dt):
+        return e_tau / dt
+
     # served form at a fixed RMSE: N per request from the pilot variances
     # (balanced choice, stat^2 <= a^2/2 at every node), plain vs eps = 1e-2 CV
     a_t = 2e-3
@@ -667,13 +753,17 @@ def run_c3(args):
         fixed[name] = {"n_paths": n_req, "seconds": secs, "nodes_per_s": len(cal_nodes) / secs,
                        "rmse_vs_exact": float(np.sqrt(np.mean((mean - u) ** 2)))}
     fixed["cv_speedup_nodes_per_s"] = fixed["cv_eps1e-2"]["nodes_per_s"] / fixed["plain"]["nodes_per_s"]
-    sat = serve(args.rate, args.window, 30.0, 11)
-    sat_short = serve(args.rate, args.window, 30.0, 11, pdd.PDD_SERVE_SHORTEST)
-    # capacity in requests/s: sustained rate over the mean offered request size
-    reqs = W.serving_requests(11, args.rate, args.window)
-    mean_req = np.mean([r["n_nodes"] * r["n_paths"] * 0.12 / r["dt"] for r in reqs])
-    cap = cal_rate / mean_req
-    steady = serve(0.7 * cap, max(30.0, args.window), 90.0, 12)
+    deadline = args.deadline
+    sat = serve(args.rate, args.window, 30.0, 11, pdd.PDD_SERVE_EARLIEST_DEADLINE,
+                deadline=deadline, steps_of=steps_of)
+    sat_fair = serve(args.rate, args.window, 30.0, 11, deadline=deadline, steps_of=steps_of)
+    sat_short = serve(args.rate, args.window, 30.0, 11, pdd.PDD_SERVE_SHORTEST, deadline=deadline,
+                      steps_of=steps_of)
+    # steady state: arrivals whose offered path-steps/s are 0.7x the served rate
+    probe = W.serving_requests(12, 100.0, 100.0)
+    mean_req = float(np.mean([r["n_nodes"] * r["n_paths"] * steps_of(r["dt"]) for r in probe]))
+    steady_rate = 0.7 * cal_rate / mean_req
+    steady = serve(steady_rate, max(30.0, args.window), 90.0, 12, steps_of=steps_of)
     clk = clocks.stop()
     prob.close()
     ctx.close()
@@ -683,13 +773,16 @@ def run_c3(args):
             "config": {"workload": "serving, Poisson arrivals over the 2D CFG0 problem; "
                                    "1-4096 nodes, 1e3-1e6 paths (log-uniform), dt in "
                                    "{1e-2,1e-3,1e-4}, eps in {none,1e-1,1e-2}; max_active 32, "
-                                   "max_queue 64, quantum 8e9 path-steps"},
-            "saturation": sat, "saturation_shortest_first": sat_short,
-            "at_0.7x_capacity": steady,
+                                   "max_queue 64, quantum 8e9 path-steps, admission deadline "
+                                   f"{deadline:g} s at the offered rate (earliest-deadline "
+                                   "policy; fair shares and shortest-first beside it)"},
+            "saturation": sat, "saturation_fair_shares": sat_fair,
+            "saturation_shortest_first": sat_short,
+            "at_0.7x_served_rate": steady,
             "served_rate_one_request_path_steps_per_s": cal_rate,
+            "expected_exit_time": e_tau,
             "fixed_rmse_served": {"target_rmse": a_t, **fixed},
-            "mean_request_path_steps_est": float(mean_req),
-            "capacity_requests_per_s_est": cap, "clocks": clk}
+            "mean_request_path_steps": mean_req, "clocks": clk}
 
 
 def run_c4(args):
@@ -952,6 +1045,96 @@ def run_fit(args):
     return out
 
 
+def run_cascade(args):
+    """The cascade Algorithm 4 schedules, run (Algorithm 5's nodal loop) on
+    the 256 interfacial nodes of the 2D problem: Algorithm 3 fit (100 time
+    steps in [1e-3, 1e-2], 10^4 paths each, psi from w = sin 3pi x sin 2pi y;
+    nodes within the shrinkage layer at some h of the cloud cannot be fitted
+    and are left out),
+    kappa measured, the schedule from a0, every level's balanced (h, N) per
+    node, all levels in one launch; against PlainPDD(a0) run the same way.
+    The previous iterate of tolerance a is synthetic, v = u + (a/2) w."""
+    import numpy as np
+    import torch
+
+    from paper_1512_02818_gb300 import cascade as C
+    from paper_1512_02818_gb300 import pdd
+    from paper_1512_02818_gb300 import workloads as W
+    ctx = pdd.Context(0)
+    torch.cuda.set_stream(ctx.stream)
+    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    w_slot = 7
+    w = W.control_grid(0, GRID_N, 1.0) - W.control_grid(0, GRID_N, 0.0)
+    prob.set_control_grid(w_slot, w)
+    nodes = W.workload_nodes("c1")
+    u = W.exact_u(0, nodes.astype(np.float64))
+    n_fit = 10_000
+    t0 = time.perf_counter()
+    fit = prob.fit_constants(nodes, n_fit, 1e-3, 1e-2, 100, grid_id=w_slot, stream_tag_base=200)
+    fit_s = time.perf_counter() - t0
+    fit_steps = float((fit["cloud"][:, :, 3] / fit["cloud"][:, :, 0]).sum() * n_fit)
+    # kappa: per-step time of the control-variate and plain kernels on these nodes
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).cuda() for j in range(2)]
+    rate = {}
+    for name, gid in (("plain", pdd.PDD_CV_NONE), ("cv", w_slot)):
+        prob.estimate(cols, 20000, 1e-3, grid_id=gid)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        rr = prob.estimate(cols, 20000, 1e-3, grid_id=gid)
+        torch.cuda.synchronize()
+        rate[name] = float((rr["mean_steps"].cpu().numpy() * 20000).sum()) / (
+            time.perf_counter() - t1)
+    kappa = rate["plain"] / rate["cv"]
+    a0 = args.a0
+    # nodes inside the shrinkage layer at some h of the cloud cannot be fitted
+    ok, fit, nodes = C.fitted_subset(fit, nodes)
+    u = u[ok]
+    a, sp = pdd.pdd_schedule(fit["K"], fit["beta"], fit["alpha"], fit["V_phi"], fit["V_psi"],
+                             fit["rho_phi_psi"], 1.0, kappa, a0, max_levels=6)
+    for j in range(len(a) - 1):  # level j reads the iterate of tolerance a[j+1]
+        prob.set_control_grid(j, W.control_grid(0, GRID_N, a[j + 1] / 2.0))
+    levels = C.plan_levels(fit, a)
+    C.run_levels(prob, nodes, C.plan_levels(fit, a), n_pilot=200)  # warm-up (kernel loads)
+    run = C.run_levels(prob, nodes, levels)
+    summ = C.summary(levels, run, u, kappa, fit, a0)
+    plain_lv = C.plan_levels(fit, [a0])
+    C.run_levels(prob, nodes, C.plan_levels(fit, [a0]), n_pilot=200, n_max=1000)  # warm-up
+    plain = C.run_levels(prob, nodes, plain_lv)
+    plain_obs = plain["levels"][0]["path_steps"]
+    out = {"workload": "cascade", "metric": METRIC, "unit": UNIT, "dtype": "f32",
+           "data": "synthetic",
+           "value": (sum(o["path_steps"] for o in run["levels"])) / run["wall_s"],
+           "config": {"workload": "Algorithm 4 schedule run as one launch (Algorithm 5 nodal "
+                                  "loop), 256 nodes of the 2D problem, target a0; previous "
+                                  "iterates v = u + (a_{j+1}/2) sin 3pi x sin 2pi y on 129^2",
+                      "a0": a0, "q": 2.0, "delta": 1.0, "fit_paths_per_h": n_fit,
+                      "fit_time_steps": 100, "nodes_fitted": int(ok.sum()),
+                      "nodes_left_out": int((~ok).sum())},
+           "fit": {"seconds": fit_s, "path_steps": fit_steps,
+                   "median_beta": float(np.median(fit["beta"])),
+                   "median_V_phi": float(np.median(fit["V_phi"])),
+                   "median_E_tau": float(np.median(fit["E_tau"]))},
+           "kappa": kappa,
+           "schedule": {"tolerances": [float(x) for x in a],
+                        "predicted_step_speedups": [float(x) for x in sp]},
+           "levels": summ["rows"],
+           "cascade": {"wall_s": run["wall_s"], "status": run["status"],
+                       "pilot_wall_s": run["pilot_s"],
+                       "pilot_path_steps": run["pilot_path_steps"],
+                       "pred_cost": summ["pred_cost"], "obs_cost": summ["obs_cost"],
+                       "pred_cumulative_speedup": summ["pred_cumulative_speedup"]},
+           "plain_a0": {"wall_s": plain["wall_s"], "status": plain["status"],
+                        "pred_path_steps": C.predicted_plain_steps(fit, a0),
+                        "obs_path_steps": plain_obs,
+                        "rmse_vs_exact": float(np.sqrt(np.mean(
+                            (plain["levels"][0]["estimate"] - u) ** 2)))},
+           "obs_cumulative_speedup": plain_obs / summ["obs_cost"],
+           "wall_speedup": plain["wall_s"] / run["wall_s"]}
+    prob.close()
+    ctx.close()
+    return out
+
+
 def run_mlmc(args):
     """Multilevel Monte Carlo (pdd_mlmc) on the 256-node 2D workload at a fixed
     RMSE, plain and with the eps = 1e-2 control grid, against the single-level
@@ -1035,7 +1218,7 @@ def main():
         if rank == 0:
             fn = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "c4": run_c4,
                   "fit": run_fit, "mlmc": run_mlmc, "paper": run_paper,
-                  "peaks": run_peaks}[args.workload]
+                  "peaks": run_peaks, "cascade": run_cascade}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":

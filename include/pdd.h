@@ -65,6 +65,10 @@ typedef enum {
   PDD_ERR_NOT_READY = -6, /* poll: request still running */
   PDD_ERR_CANCELLED = -7, /* poll: request was cancelled */
   PDD_ERR_OVERFLOW = -8,  /* a score left the fixed-point range |score| < 32768 */
+  PDD_ERR_BOUNDS = -9,    /* bounds-checked build only: a kernel index left its buffer
+                             (the message names the checks that failed)               */
+  PDD_ERR_DEADLINE = -10, /* submit: the request cannot finish within the server's
+                             deadline after the work already queued and running       */
   PDD_WARN_TRUNCATED = 1, /* results valid, but some paths hit max_steps */
   PDD_WARN_NOT_CONVERGED = 2 /* pdd_mlmc: results valid, stopping test not met */
 } pdd_status;
@@ -406,6 +410,34 @@ typedef struct {
 int pdd_schedule(const pdd_schedule_args* args, double* a, double* speedup, int max_levels,
                  int* n_levels);
 
+/* Balanced simulation per node (Definition "Balanced MC simulation",
+   eq. F:N_y_h): at tolerance a with confidence factor q and weak order delta,
+     h_i = (a / (2 |beta_i|))^(1/delta)   (bias = a/2),
+     N_i = ceil(4 q^2 V_i / a^2)           (statistical error = a/2),
+   h_i clamped to [h_min, h_max] (beta_i = 0 gives h_max) and N_i to
+   [n_min, n_max].  V_i is the variance of the score the level runs: V[phi]
+   for a plain level, V[phi + xi] with a control variate.  Host computation,
+   no GPU; host arrays of n_nodes (beta, var in; h, n_paths out).
+   PDD_ERR_INVALID on bad arguments.                                         */
+int pdd_balanced_plan(int64_t n_nodes, double a, double q, double delta, const double* beta,
+                      const double* var, double h_min, double h_max, int64_t n_min,
+                      int64_t n_max, double* h, int64_t* n_paths);
+
+/* The scheduling model's prediction for one level of the cascade (Algorithm 4
+   objective, eq. F:Sensitivity_formula): the level at tolerance aj that uses
+   the control variate of the coarser level at tolerance a (a <= 0: a plain
+   level).  Per node i, with r_i^2(a) as in pdd_schedule:
+     rho2[i] = max(r_i^2(a) - |alpha_i r_i(a) / beta_i| aj, 0), the predicted
+               rho^2[phi_h, xi_h] (0 for a plain level);
+     cost[i] = K_i V_i[phi] w_i / aj^(2 + 1/delta), the predicted path-steps
+               (eq. F:Pointwise_cost), w_i = 1 - r_i^2(a) + |alpha_i r_i(a) /
+               beta_i| aj for a controlled level (multiply by kappa for its
+               cost in plain-step units) and 1 for a plain one.
+   Host computation; host arrays of s->n_nodes.  PDD_ERR_INVALID on bad
+   arguments.                                                               */
+int pdd_schedule_predict(const pdd_schedule_args* s, double a, double aj, double* rho2,
+                         double* cost);
+
 /* Autotuner: runs `sample` (device coordinates) under candidate launch shapes
    (128/256/512 threads per block, full and half occupancy), times each with
    CUDA events on the context's stream, and keeps the fastest as the context's
@@ -435,32 +467,63 @@ typedef struct {
                                   PDD_SERVE_FAIR (0): equal shares; PDD_SERVE_SHORTEST (1):
                                   requests with the least remaining work first, each up to
                                   all its remaining paths, until the quantum is spent (less
-                                  latency for small requests; large ones wait under overload) */
+                                  latency for small requests; large ones wait under overload);
+                                  PDD_SERVE_EARLIEST_DEADLINE (2): the same fill in submission
+                                  order (every request has the relative deadline deadline_s),
+                                  under which the deadline admission bounds every admitted
+                                  request's completion by deadline_s, as far as the predicted
+                                  work and rate hold */
   int32_t reserved;            /* 0 */
+  double deadline_s;           /* > 0: admission by predicted work -- pdd_submit refuses
+                                  (PDD_ERR_DEADLINE) a request whose predicted path-steps,
+                                  added to the predicted remaining path-steps of every
+                                  queued and running request, would take longer than
+                                  deadline_s at the server's measured rate (a guarantee under
+                                  PDD_SERVE_EARLIEST_DEADLINE, an estimate under the other
+                                  policies); 0: no deadline */
+  double rate_hint;            /* path-steps/s assumed until the server has measured its own
+                                  rate over retired launches (0: 1e11) */
 } pdd_server_desc;
 #define PDD_SERVE_FAIR 0
 #define PDD_SERVE_SHORTEST 1
+#define PDD_SERVE_EARLIEST_DEADLINE 2
 
 typedef struct {
   int64_t submitted, admitted, rejected_busy, rejected_invalid, rejected_nomem;
   int64_t completed, cancelled, failed, launches, pending, active;
   int64_t path_steps;  /* Euler steps executed by retired launches, whether or not
                           their requests later completed */
+  int64_t rejected_deadline;      /* refused by the deadline (PDD_ERR_DEADLINE) */
+  int64_t completed_path_steps;   /* Euler steps of completed requests (their results'
+                                     mean exit index x paths): goodput = this / path_steps */
+  int64_t backlog_path_steps;     /* predicted path-steps still to run for queued and
+                                     running requests */
+  int64_t rate_path_steps_per_s;  /* the rate admission currently assumes */
 } pdd_server_stats;
 
 int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** out);
 /* Copies the request (coordinates from host or device memory, read before the
-   call returns) and queues it; never waits for the GPU.  PDD_ERR_BUSY when
-   max_queue requests are pending (retry or shed), PDD_ERR_NOMEM when the
+   call returns) and queues it.  Its predicted work is n_nodes x n_paths x
+   (expected exit index at its dt); the expected exit index of each (problem,
+   dt) comes from a pilot launch (64 paths from each of up to 128 of the
+   request's nodes, plain estimator) that the first request with that pair
+   runs before this call returns -- the only time pdd_submit waits for the
+   GPU -- and is refined with the exit indices of every completed request.
+   PDD_ERR_BUSY when max_queue requests are pending (retry or shed),
+   PDD_ERR_DEADLINE when desc.deadline_s is set and the request's predicted
+   work would not finish within it after the backlog, PDD_ERR_NOMEM when the
    request can never fit the arena, PDD_ERR_INVALID for malformed requests
-   (EMIT_PATHS is not served).  *ticket identifies the request.             */
+   (EMIT_PATHS is not served).  Each refusal is counted apart in the
+   statistics.  *ticket identifies the request.                             */
 int pdd_submit(pdd_server* server, pdd_problem* problem, const pdd_estimate_args* args,
                uint64_t* ticket);
 /* Waits up to timeout_us (0: do not wait) for the request.  PDD_OK: results
    copied into *out (host or device per out->on_device) and the ticket is
    released; PDD_ERR_NOT_READY / PDD_ERR_TIMEOUT: still running (ticket kept);
    PDD_ERR_CANCELLED: cancelled (ticket released); other errors: the request
-   failed (ticket released).                                                 */
+   failed (ticket released) -- PDD_ERR_OVERFLOW (or PDD_ERR_BOUNDS in the
+   bounds-checked build) fails every request with a slice in the launch whose
+   error word was set.                                                       */
 int pdd_poll(pdd_server* server, uint64_t ticket, pdd_node_stats* out, int timeout_us);
 /* Stops issuing the request's paths; its memory is released once no launch
    in flight uses it; pdd_poll then returns PDD_ERR_CANCELLED.               */

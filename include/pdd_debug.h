@@ -38,6 +38,17 @@ int pdd_debug_normals(uint64_t seed, uint32_t tag, uint32_t node, uint32_t path,
    per thread; synchronous.  iters in [1, 2^24].                            */
 int pdd_debug_issue_rate(int kind, int iters, double* ops_per_s, double* ms);
 
+/* Self-test of the bounds checks (no counterpart in the paper).  A one-thread
+   kernel feeds the checks of the bounds-checked build (libpdd_bounds.so,
+   compiled with -DPDD_DEBUG_BOUNDS=1) one failing case of each kind -- a
+   grid cell index of -1, and false conditions for the path-index, record,
+   exit-ring and per-path-output checks -- without performing any of the
+   guarded accesses, and returns the resulting error word in *bits (host
+   pointer): 62 (all five bounds bits) in the bounds-checked build, 0 in the
+   release build, whose checks compile to nothing.  Synchronous; allocates
+   and frees one device word.                                                */
+int pdd_debug_bounds_selftest(uint32_t* bits);
+
 #ifdef __cplusplus
 }
 #endif

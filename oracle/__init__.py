@@ -359,6 +359,11 @@ def fit_constants(kind, nodes, n_paths, h_min, h_max, n_h, delta=1.0, q=2.0, see
         out["rho_phi_psi"][i] = out["cov_phi_psi"][i] / np.sqrt(out["V_phi"][i] * out["V_psi"][i])
         # nodal cost constant of eq. F:Pointwise_cost
         out["K"][i] = 4 * q * q * out["E_tau"][i] * (2 * abs(out["beta"][i])) ** (1 / delta)
+        # every path left at k = 0 at some h (zero sample variance: the node is
+        # inside the shrinkage layer there): the fitted model does not hold
+        if np.any(~(cloud[i, :, 2] > 0)):
+            for k in out:
+                out[k][i] = np.nan
     out["cloud"] = cloud
     return out
 
@@ -384,6 +389,10 @@ def schedule(K, beta, alpha, V_phi, V_psi, rho, delta, kappa, a0, min_speedup=1.
     from scipy import optimize
     K, beta, alpha, V_phi, V_psi, rho = (np.asarray(v, dtype=np.float64)
                                          for v in (K, beta, alpha, V_phi, V_psi, rho))
+    # nodes with constants Algorithm 3 could not fit (NaN) are left out
+    use = (np.isfinite(K) & np.isfinite(beta) & np.isfinite(alpha) & np.isfinite(V_phi)
+           & np.isfinite(V_psi) & np.isfinite(rho) & (V_phi > 0) & (beta != 0))
+    K, beta, alpha, V_phi, V_psi, rho = (v[use] for v in (K, beta, alpha, V_phi, V_psi, rho))
     plain = float(np.sum(K * V_phi))
     c = V_psi * (1 - rho * rho) / (4 * V_phi)
     amax = float(np.max(1 / np.sqrt(c[c > 0])))

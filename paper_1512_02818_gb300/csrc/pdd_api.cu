@@ -30,6 +30,23 @@ void set_error(const char* fmt, ...) {
   g_last_error = buf;
 }
 
+int error_word_status(unsigned err, const char* who) {
+  if (err & kErrBoundsAll) {
+    set_error("%s: bounds check failed (error bits 0x%x:%s%s%s%s%s)", who, err,
+              (err & kErrBoundsGrid) ? " grid cell" : "",
+              (err & kErrBoundsIndex) ? " path index" : "",
+              (err & kErrBoundsRecord) ? " node record" : "",
+              (err & kErrBoundsRing) ? " exit ring" : "",
+              (err & kErrBoundsEmit) ? " per-path output" : "");
+    return PDD_ERR_BOUNDS;
+  }
+  if (err & kErrOverflow) {
+    set_error("%s: a score left the fixed-point range |score| < 32768", who);
+    return PDD_ERR_OVERFLOW;
+  }
+  return PDD_OK;
+}
+
 static int cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: CUDA error %d (%s)", what, (int)e, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? PDD_ERR_NOMEM : PDD_ERR_CUDA;
@@ -360,6 +377,12 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
   pa.total = begin;
 
   StatPtrs sp[PDD_MAX_LEVELS];
+  uint32_t lvl_nodes[PDD_MAX_LEVELS];
+  double lvl_kappa[PDD_MAX_LEVELS];
+  for (int l = 0; l < n_levels; ++l) {
+    lvl_nodes[l] = (uint32_t)levels[l].n_nodes;
+    lvl_kappa[l] = levels[l].kappa > 0.0 ? levels[l].kappa : 1.0;
+  }
   for (int l = 0; l < n_levels; ++l) {
     const pdd_node_stats& o = outs[l];
     double* const user_d[12] = {o.mean_phi, o.var_phi, o.mean_cv, o.var_cv, o.cov_phi_xi,
@@ -387,17 +410,9 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
     int blocks = 0;
     e = launch_paths(p->desc.kind, p->desc.precision, cv, pa, c->num_sms, st, &blocks);
     if (e != cudaSuccess) return e;
-    for (int l = 0; l < n_levels; ++l) {
-      if (levels[l].n_nodes == 0) continue;
-      const double kappa = levels[l].kappa > 0.0 ? levels[l].kappa : 1.0;
-      e = launch_finalize(acc + (size_t)rec_base[l] * kAccWords, (uint32_t)levels[l].n_nodes,
-                          kappa, sp[l], st);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return launch_finalize_levels(acc, n_levels, rec_base, lvl_nodes, lvl_kappa, sp, st);
   };
-  int n_launch = 1;
-  for (int l = 0; l < n_levels; ++l) n_launch += levels[l].n_nodes > 0;
+  const int n_launch = 2;  // the path kernel and one finalisation for every level
 
   // host inputs
   for (int l = 0; l < n_levels; ++l) {
@@ -458,13 +473,8 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
     PDD_CUDA(launch_paths(p->desc.kind, p->desc.precision, cv, pa, c->num_sms, c->stream, &blocks),
              "path kernel launch");
     if (c->timing) PDD_CUDA(cudaEventRecord(ev1, c->stream), "cudaEventRecord");
-    for (int l = 0; l < n_levels; ++l) {
-      if (levels[l].n_nodes == 0) continue;
-      const double kappa = levels[l].kappa > 0.0 ? levels[l].kappa : 1.0;
-      PDD_CUDA(launch_finalize(acc + (size_t)rec_base[l] * kAccWords,
-                               (uint32_t)levels[l].n_nodes, kappa, sp[l], c->stream),
-               "finalize launch");
-    }
+    PDD_CUDA(launch_finalize_levels(acc, n_levels, rec_base, lvl_nodes, lvl_kappa, sp, c->stream),
+             "finalize launch");
   }
   if (c->timing) c->events.emplace_back(ev0, ev1);
   c->launches += n_launch;
@@ -495,10 +505,7 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
   PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync(header)");
   PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-  if (h.err & kErrOverflow) {
-    set_error("%s: a score left the fixed-point range |score| < 32768", who);
-    return PDD_ERR_OVERFLOW;
-  }
+  if (h.err != 0u) return error_word_status(h.err, who);
   if (h.cursor < pa.total) {
     set_error("%s: internal error, %llu of %llu paths scheduled", who, h.cursor, pa.total);
     return PDD_ERR_CUDA;
@@ -890,10 +897,7 @@ int pdd_accumulate(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_off
   PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync(header)");
   PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-  if (h.err & kErrOverflow) {
-    set_error("pdd_accumulate: a score left the fixed-point range |score| < 32768");
-    return PDD_ERR_OVERFLOW;
-  }
+  if (h.err != 0u) return error_word_status(h.err, "pdd_accumulate");
   if (h.trunc_total > 0) {
     set_error("pdd_accumulate: %llu paths hit max_steps", h.trunc_total);
     return PDD_WARN_TRUNCATED;
@@ -1036,10 +1040,7 @@ static int coupled_status(pdd_ctx* c, const char* who) {
   PDD_CUDA(cudaMemcpyAsync(&h, c->ws, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync(header)");
   PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-  if (h.err & kErrOverflow) {
-    set_error("%s: a score left the fixed-point range |score| < 32768", who);
-    return PDD_ERR_OVERFLOW;
-  }
+  if (h.err != 0u) return error_word_status(h.err, who);
   if (h.trunc_total > 0) {
     set_error("%s: %llu paths hit max_steps", who, h.trunc_total);
     return PDD_WARN_TRUNCATED;

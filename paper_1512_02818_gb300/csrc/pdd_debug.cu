@@ -110,3 +110,42 @@ extern "C" int pdd_debug_normals(uint64_t seed, uint32_t tag, uint32_t node, uin
     normals_kernel<double><<<blocks, 256>>>(seed, tag, node, path, first, count, out_f64);
   return finish(cudaGetLastError());
 }
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounds checks: every check fails once, nothing is accessed.
+// ---------------------------------------------------------------------------
+namespace {
+struct ErrOnly {
+  unsigned* err;
+};
+__global__ void bounds_selftest_kernel(unsigned* err) {
+  const ErrOnly a{err};
+  (void)a;
+  (void)pdd::cell_in_table(err, -1, 0, 0, 9);
+  (void)PDD_IN_BOUNDS(a, false, pdd::kErrBoundsIndex);
+  (void)PDD_IN_BOUNDS(a, false, pdd::kErrBoundsRecord);
+  (void)PDD_IN_BOUNDS(a, false, pdd::kErrBoundsRing);
+  (void)PDD_IN_BOUNDS(a, false, pdd::kErrBoundsEmit);
+}
+}  // namespace
+
+extern "C" int pdd_debug_bounds_selftest(uint32_t* bits) {
+  if (!bits) {
+    pdd::set_error("pdd_debug_bounds_selftest: bits is NULL");
+    return PDD_ERR_INVALID;
+  }
+  unsigned* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(unsigned));
+  if (e == cudaSuccess) {
+    bounds_selftest_kernel<<<1, 1>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(bits, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) {
+    pdd::set_error("pdd_debug_bounds_selftest: %s", cudaGetErrorString(e));
+    return PDD_ERR_CUDA;
+  }
+  return PDD_OK;
+}

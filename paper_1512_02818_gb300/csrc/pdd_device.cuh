@@ -288,6 +288,33 @@ __device__ __forceinline__ void project_box(T* p, int dim) {
 // clamped to [0, n-2], multilinear weights.  2D tables are float2 (gx, gy),
 // 3D tables float4 (gx, gy, gz, 0) so every corner is one 8- or 16-byte load.
 // ---------------------------------------------------------------------------
+// Bounds-checked build (-DPDD_DEBUG_BOUNDS=1): `ok` false sets `bit` in the
+// launch's error word and the caller skips the guarded access; the host turns
+// a non-zero word into PDD_ERR_BOUNDS.  The release build evaluates nothing.
+__device__ __forceinline__ bool bounds_ok(unsigned* err, bool ok, unsigned bit) {
+  if (!ok) atomicOr(err, bit);
+  return ok;
+}
+#if PDD_DEBUG_BOUNDS
+#define PDD_IN_BOUNDS(a, ok, bit) ::pdd::bounds_ok((a).err, (ok), (bit))
+#else
+#define PDD_IN_BOUNDS(a, ok, bit) true
+#endif
+
+// Bounds-checked build: a cell index outside [0, n-2] sets kErrBoundsGrid in
+// the launch's error word (`err`) and the lookup is skipped.  The release
+// build checks nothing (the indices are clamped by construction).
+__device__ __forceinline__ bool cell_in_table(unsigned* err, int ix, int iy, int iz, int n) {
+#if PDD_DEBUG_BOUNDS
+  const bool ok = ix >= 0 && ix <= n - 2 && iy >= 0 && iy <= n - 2 && iz >= 0 && iz <= n - 2 &&
+                  n >= 2;
+  return err ? bounds_ok(err, ok, kErrBoundsGrid) : ok;
+#else
+  (void)err; (void)ix; (void)iy; (void)iz; (void)n;
+  return true;
+#endif
+}
+
 template <class T>
 __device__ __forceinline__ int cell_of(T t, int n, T& frac) {
   int i = (int)floor(t);
@@ -298,10 +325,14 @@ __device__ __forceinline__ int cell_of(T t, int n, T& frac) {
 
 template <class T>
 __device__ __forceinline__ void grid_grad_2d(const float2* __restrict__ G, int n, T x, T y, T& gx,
-                                             T& gy) {
+                                             T& gy, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy;
   const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy);
+  if (!cell_in_table(err, ix, iy, 0, n)) {
+    gx = gy = T(0);
+    return;
+  }
   const float2* p = G + (size_t)iy * n + ix;
   const float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + n), d = __ldg(p + n + 1);
   const T lx0 = (T)a.x + fx * ((T)b.x - (T)a.x), lx1 = (T)c.x + fx * ((T)d.x - (T)c.x);
@@ -312,10 +343,14 @@ __device__ __forceinline__ void grid_grad_2d(const float2* __restrict__ G, int n
 
 template <class T>
 __device__ __forceinline__ void grid_grad_3d(const float4* __restrict__ G, int n, T x, T y, T z,
-                                             T& gx, T& gy, T& gz) {
+                                             T& gx, T& gy, T& gz, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy, fz;
   const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy), iz = cell_of(z * s, n, fz);
+  if (!cell_in_table(err, ix, iy, iz, n)) {
+    gx = gy = gz = T(0);
+    return;
+  }
   const size_t nn = (size_t)n * n;
   const float4* p = G + (size_t)iz * nn + (size_t)iy * n + ix;
   T acc[3][2][2];  // [component][y corner][z corner] after the x lerp
@@ -368,9 +403,11 @@ __host__ __device__ __forceinline__ size_t cell_table_offset(int n, int dim) {
 // 32-byte load through the non-coherent (read-only) path: one 256-bit vector
 // load per record chunk, so a lane's chunk is one full sector.  `p` must be
 // 32-byte aligned (records start at multiples of 32 bytes of a 256-byte
-// aligned table).
+// aligned table).  The tables do not change while a kernel runs, so the load
+// is a pure function of its address (not volatile): the compiler may schedule
+// it as early as the address is known.
 __device__ __forceinline__ void ldg_v8(const float4* p, float4& a, float4& b) {
-  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z),
                  "=f"(b.w)
                : "l"(p));
@@ -378,10 +415,14 @@ __device__ __forceinline__ void ldg_v8(const float4* p, float4& a, float4& b) {
 
 template <class T>
 __device__ __forceinline__ void grid_cells_2d(const float4* __restrict__ C, int n, T x, T y,
-                                              T& gx, T& gy) {
+                                              T& gx, T& gy, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy;
   const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy);
+  if (!cell_in_table(err, ix, iy, 0, n)) {
+    gx = gy = T(0);
+    return;
+  }
   const float4* p = C + 2 * ((size_t)iy * (n - 1) + ix);
   float4 a, b;
   ldg_v8(p, a, b);
@@ -408,10 +449,14 @@ __device__ __forceinline__ float half_hi(float w) {
 
 template <class T>
 __device__ __forceinline__ void grid_cells_3d(const float4* __restrict__ C, int n, T x, T y, T z,
-                                              T& gx, T& gy, T& gz) {
+                                              T& gx, T& gy, T& gz, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy, fz;
   const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy), iz = cell_of(z * s, n, fz);
+  if (!cell_in_table(err, ix, iy, iz, n)) {
+    gx = gy = gz = T(0);
+    return;
+  }
   const size_t m = (size_t)(n - 1);
   const float4* p = C + 4 * (((size_t)iz * m + iy) * m + ix);
   float4 a, b, c, d;  // words 0-3, 4-7, 8-11, 12-15

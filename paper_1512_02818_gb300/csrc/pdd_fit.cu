@@ -155,6 +155,18 @@ extern "C" int pdd_fit_constants(pdd_problem* p, const pdd_fit_args* a, pdd_fit_
   for (size_t j = 0; j < M; ++j) x[j] = std::pow(hs[j], a->delta);
   auto stat = [&](size_t j, int f, size_t i) { return hstat[(j * kF + f) * n + i]; };
   for (size_t i = 0; i < n; ++i) {
+    // A node whose paths all leave at k = 0 at some time step of the cloud
+    // (zero sample variance: it lies inside the shrinkage layer c0 sqrt(h) of
+    // the boundary there) is outside the model E[eta_h] = E[eta_0] + B h^delta
+    // the fits assume: its constants are NaN and the schedule leaves it out.
+    bool degenerate = false;
+    for (size_t j = 0; j < M; ++j) degenerate |= !(stat(j, 1, i) > 0.0);
+    if (degenerate) {
+      double* const outs[9] = {out->E_phi, out->beta, out->V_phi, out->alpha, out->E_tau,
+                               out->K, out->cov_phi_psi, out->V_psi, out->rho_phi_psi};
+      for (double* o : outs)
+        if (o) o[i] = NAN;
+    }
     double e_phi, beta, v_phi, alpha, e_tau, slope, cov0 = NAN, v_psi = NAN;
     for (size_t j = 0; j < M; ++j) y[j] = stat(j, 0, i);
     ols(x, y, &e_phi, &beta);
@@ -169,15 +181,17 @@ extern "C" int pdd_fit_constants(pdd_problem* p, const pdd_fit_args* a, pdd_fit_
       gamma_identity(x, y, &v_psi, &slope);
     }
     const double K = 4.0 * a->q * a->q * e_tau * std::pow(2.0 * std::fabs(beta), 1.0 / a->delta);
-    if (out->E_phi) out->E_phi[i] = e_phi;
-    if (out->beta) out->beta[i] = beta;
-    if (out->V_phi) out->V_phi[i] = v_phi;
-    if (out->alpha) out->alpha[i] = alpha;
-    if (out->E_tau) out->E_tau[i] = e_tau;
-    if (out->K) out->K[i] = K;
-    if (out->cov_phi_psi) out->cov_phi_psi[i] = cov0;
-    if (out->V_psi) out->V_psi[i] = v_psi;
-    if (out->rho_phi_psi) out->rho_phi_psi[i] = cov0 / std::sqrt(v_phi * v_psi);
+    if (!degenerate) {
+      if (out->E_phi) out->E_phi[i] = e_phi;
+      if (out->beta) out->beta[i] = beta;
+      if (out->V_phi) out->V_phi[i] = v_phi;
+      if (out->alpha) out->alpha[i] = alpha;
+      if (out->E_tau) out->E_tau[i] = e_tau;
+      if (out->K) out->K[i] = K;
+      if (out->cov_phi_psi) out->cov_phi_psi[i] = cov0;
+      if (out->V_psi) out->V_psi[i] = v_psi;
+      if (out->rho_phi_psi) out->rho_phi_psi[i] = cov0 / std::sqrt(v_phi * v_psi);
+    }
     if (out->cloud)
       for (size_t j = 0; j < M; ++j) {
         double* c = out->cloud + (i * M + j) * 6;
@@ -202,12 +216,21 @@ struct SchedData {
   double p;  // 2 + 1/delta
 };
 
+// Nodes the schedule uses: finite fitted constants, V[phi] > 0 and beta != 0
+// (a node Algorithm 3 could not fit has NaN constants and is left out).
+bool usable(const pdd_schedule_args& s, int64_t i) {
+  return std::isfinite(s.K[i]) && std::isfinite(s.beta[i]) && std::isfinite(s.alpha[i]) &&
+         std::isfinite(s.V_phi[i]) && std::isfinite(s.V_psi[i]) &&
+         std::isfinite(s.rho_phi_psi[i]) && s.V_phi[i] > 0.0 && s.beta[i] != 0.0;
+}
+
 // Predicted cost of the level with tolerance aj using the control variate of
 // the coarser level with tolerance a (the minimised objective of Algorithm 4).
 double sched_cost(const SchedData& d, double a, double aj) {
   const pdd_schedule_args& s = *d.a;
   double tot = 0.0;
   for (int64_t i = 0; i < s.n_nodes; ++i) {
+    if (!usable(s, i)) continue;
     double r2 = 1.0 - s.V_psi[i] * a * a * (1.0 - s.rho_phi_psi[i] * s.rho_phi_psi[i]) /
                           (4.0 * s.V_phi[i]);
     if (r2 < 0.0) r2 = 0.0;
@@ -230,11 +253,18 @@ extern "C" int pdd_schedule(const pdd_schedule_args* s, double* a, double* speed
   }
   SchedData d{s, 2.0 + 1.0 / s->delta};
   double plain = 0.0, amax = 0.0;
+  int64_t n_usable = 0;
   for (int64_t i = 0; i < s->n_nodes; ++i) {
+    if (!usable(*s, i)) continue;
+    ++n_usable;
     plain += s->K[i] * s->V_phi[i];
     const double c = s->V_psi[i] * (1.0 - s->rho_phi_psi[i] * s->rho_phi_psi[i]) /
                      (4.0 * s->V_phi[i]);
     if (c > 0) amax = std::max(amax, 1.0 / std::sqrt(c));
+  }
+  if (n_usable == 0) {
+    set_error("pdd_schedule: no node has usable fitted constants");
+    return PDD_ERR_INVALID;
   }
   const double min_s = s->min_speedup > 0 ? s->min_speedup : 1.5;
   a[0] = s->a0;
@@ -284,5 +314,65 @@ extern "C" int pdd_schedule(const pdd_schedule_args* s, double* a, double* speed
     aj = anext;
   }
   *n_levels = J;
+  return PDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Balanced simulation per node (Definition "Balanced MC simulation",
+// eq. F:N_y_h) and the scheduling model's per-level prediction (Algorithm 4,
+// eq. F:Sensitivity_formula), used to run the levels Algorithm 4 schedules
+// (Algorithm 5: "for node x_i and a_j, determine h and N").
+// ---------------------------------------------------------------------------
+extern "C" int pdd_balanced_plan(int64_t n_nodes, double a, double q, double delta,
+                                 const double* beta, const double* var, double h_min,
+                                 double h_max, int64_t n_min, int64_t n_max, double* h,
+                                 int64_t* n_paths) {
+  if (n_nodes < 0 || !(a > 0) || !std::isfinite(a) || !(q > 0) || !(delta > 0) ||
+      !(h_min > 0) || !(h_max >= h_min) || !std::isfinite(h_max) || n_min < 1 ||
+      n_max < n_min || (n_nodes > 0 && (!beta || !var || !h || !n_paths))) {
+    set_error("pdd_balanced_plan: bad arguments (need a, q, delta > 0, 0 < h_min <= h_max, "
+              "1 <= n_min <= n_max, non-NULL arrays)");
+    return PDD_ERR_INVALID;
+  }
+  for (int64_t i = 0; i < n_nodes; ++i) {
+    // bias |beta| h^delta = a / 2 and statistical error q sqrt(V / N) = a / 2
+    const double b = std::fabs(beta[i]);
+    double hi = b > 0 ? std::pow(a / (2.0 * b), 1.0 / delta) : h_max;
+    if (!(hi >= h_min)) hi = h_min;  // also catches NaN
+    if (hi > h_max) hi = h_max;
+    h[i] = hi;
+    const double v = var[i] > 0 ? var[i] : 0.0;
+    const double nn = std::ceil(4.0 * q * q * v / (a * a));
+    int64_t ni = nn >= (double)n_max || !std::isfinite(nn) ? n_max : (int64_t)nn;
+    if (ni < n_min) ni = n_min;
+    n_paths[i] = ni;
+  }
+  return PDD_OK;
+}
+
+extern "C" int pdd_schedule_predict(const pdd_schedule_args* s, double a, double aj, double* rho2,
+                                    double* cost) {
+  if (!s || s->n_nodes < 1 || !s->K || !s->beta || !s->alpha || !s->V_phi || !s->V_psi ||
+      !s->rho_phi_psi || !(s->delta > 0) || !(aj > 0) || !rho2 || !cost) {
+    set_error("pdd_schedule_predict: bad arguments");
+    return PDD_ERR_INVALID;
+  }
+  const double p = 2.0 + 1.0 / s->delta;
+  const double scale = std::pow(aj, -p);
+  for (int64_t i = 0; i < s->n_nodes; ++i) {
+    const double base = s->K[i] * s->V_phi[i] * scale;  // plain cost at aj (eq. F:Pointwise_cost)
+    if (!(a > 0)) {
+      rho2[i] = 0.0;
+      cost[i] = base;
+      continue;
+    }
+    double r2 = 1.0 - s->V_psi[i] * a * a * (1.0 - s->rho_phi_psi[i] * s->rho_phi_psi[i]) /
+                          (4.0 * s->V_phi[i]);
+    if (r2 < 0.0) r2 = 0.0;
+    const double r = std::sqrt(r2);
+    const double loss = std::fabs(s->alpha[i] * r / s->beta[i]) * aj;
+    rho2[i] = std::max(r2 - loss, 0.0);
+    cost[i] = base * (1.0 - r2 + loss);
+  }
   return PDD_OK;
 }

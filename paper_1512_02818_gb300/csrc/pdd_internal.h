@@ -12,6 +12,18 @@
 namespace pdd {
 
 constexpr unsigned kErrOverflow = 1u;       // a score left the fixed-point range
+// Bits of the bounds-checked build (compiled with -DPDD_DEBUG_BOUNDS=1): an
+// index that would leave its buffer sets its bit and the access is skipped.
+// The release build computes no check and never sets them.
+constexpr unsigned kErrBoundsGrid = 2u;     // control-grid cell outside the table
+constexpr unsigned kErrBoundsIndex = 4u;    // flat path index, segment, node or path out of range
+constexpr unsigned kErrBoundsRecord = 8u;   // node record or shared-memory record slot
+constexpr unsigned kErrBoundsRing = 16u;    // exit ring over-full
+constexpr unsigned kErrBoundsEmit = 32u;    // per-path output index
+constexpr unsigned kErrBoundsAll = 62u;
+#ifndef PDD_DEBUG_BOUNDS
+#define PDD_DEBUG_BOUNDS 0
+#endif
 constexpr int kAccWords = 16;               // 64-bit words per node record
 static_assert(kAccWords == PDD_RECORD_WORDS, "node record size");
 constexpr unsigned long long kWarpBatch = 32;  // path indices a warp takes per cursor grab
@@ -116,6 +128,9 @@ struct ProblemView {
 };
 
 static_assert(PDD_MAX_GRIDS == 8, "ProblemView holds 8 grid slots");
+// Status of a launch's error word: PDD_ERR_BOUNDS (bounds-checked build) or
+// PDD_ERR_OVERFLOW with a message naming `who`, PDD_OK when no bit is set.
+int error_word_status(unsigned err, const char* who);
 bool problem_view(pdd_problem* p, ProblemView* v);
 bool ctx_view(pdd_ctx* c, int* device, int* num_sms, int* block_threads, int* max_blocks);
 pdd_ctx* problem_ctx(pdd_problem* p);
@@ -130,6 +145,11 @@ cudaError_t launch_coupled(int kind, int cv, const PathArgs& a, int num_sms, cud
                            int* blocks);
 cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, double kappa,
                             const StatPtrs& out, cudaStream_t st);
+// One launch for the records of up to kMaxSegments levels stored back to
+// back from `acc` (level l at record node_base[l]; empty levels skipped).
+cudaError_t launch_finalize_levels(const unsigned long long* acc, int n_levels,
+                                   const uint32_t* node_base, const uint32_t* n_nodes,
+                                   const double* kappa, const StatPtrs* out, cudaStream_t st);
 // Gradient table of grid values v (FP64, n^D, x fastest) into float2/float4.
 cudaError_t launch_grid_gradient(const double* v, int n, int dim, void* table, cudaStream_t st);
 // Pack D interleaved gradient components (FP64) into float2/float4.

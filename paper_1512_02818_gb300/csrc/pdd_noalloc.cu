@@ -215,10 +215,7 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   e = cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, pv.stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(pv.stream);
   if (e != cudaSuccess) return fail(e, "cudaStreamSynchronize");
-  if (h.err & kErrOverflow) {
-    set_error("pdd_estimate_nodes_noalloc: a score left the fixed-point range |score| < 32768");
-    return PDD_ERR_OVERFLOW;
-  }
+  if (h.err != 0u) return error_word_status(h.err, "pdd_estimate_nodes_noalloc");
   if (h.cursor < pa.total) {
     set_error("pdd_estimate_nodes_noalloc: internal error, %llu of %llu paths scheduled",
               h.cursor, pa.total);

@@ -70,6 +70,19 @@ struct UseCells {
       sizeof(T) == 4 && ((D == 2 && PDD_CELLS_2D) || (D == 3 && PDD_CELLS_3D));
 };
 
+// Order of a launch's flat path index inside a segment: path-major (the
+// default: g = path * n_nodes + node, so the paths in flight belong to many
+// nodes) or node-major (g = node * n_paths + path: the paths in flight start
+// from a few nodes).  Build experiment: -DPDD_NODE_MAJOR_3D=1 makes 3D
+// launches node-major.
+#ifndef PDD_NODE_MAJOR_3D
+#define PDD_NODE_MAJOR_3D 0
+#endif
+template <int D>
+struct NodeMajor {
+  static constexpr bool value = D == 3 && PDD_NODE_MAJOR_3D;
+};
+
 template <class T>
 struct LaneSeg {
   T h, sqh, thr0;
@@ -105,7 +118,29 @@ __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long
   }
   const SegArgs& sg = a.seg[si];
   const unsigned long long li = g - sg.begin;
-  if (sg.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
+  if (!PDD_IN_BOUNDS(a, si < (uint32_t)a.n_segs && g >= sg.begin && li < sg.total && g < a.total,
+                     kErrBoundsIndex)) {
+    // leave the lane on node 0, path 0 of segment 0 (in bounds); the call fails
+    s.node = s.path = s.seg = 0;
+    s.x[0] = s.x[1] = s.x[2] = T(0.5);
+    s.Y = T(1);
+    s.Z = s.Zc = s.XI = s.XIc = T(0);
+    s.k = 0;
+    if (MULTI) load_seg<T, D>(a.seg[0], ls);
+    return;
+  }
+  if (NodeMajor<D>::value) {  // consecutive indices: consecutive paths of one node
+    if (sg.total <= 0xFFFFFFFFull) {
+      const uint32_t gg = (uint32_t)li, np = (uint32_t)sg.n_paths;
+      const uint32_t nd = gg / np;
+      s.node = nd;
+      s.path = sg.path_off + (gg - nd * np);
+    } else {
+      const unsigned long long nd = li / sg.n_paths;
+      s.node = (uint32_t)nd;
+      s.path = sg.path_off + (uint32_t)(li - nd * sg.n_paths);
+    }
+  } else if (sg.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
     const uint32_t gg = (uint32_t)li, nn = (uint32_t)sg.n_nodes;
     const uint32_t p = gg / nn;
     s.node = gg - p * nn;
@@ -116,6 +151,9 @@ __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long
     s.path = sg.path_off + (uint32_t)p;
   }
   s.seg = si;
+  if (!PDD_IN_BOUNDS(a, s.node < sg.n_nodes && s.path - sg.path_off < sg.n_paths,
+                     kErrBoundsIndex))
+    s.node = 0;
   s.x[0] = (T)__ldg(sg.cx + s.node);
   s.x[1] = (T)__ldg(sg.cy + s.node);
   s.x[2] = (D == 3) ? (T)__ldg(sg.cz + s.node) : T(0);
@@ -153,6 +191,29 @@ template <class P, class T, int D, int CV, bool MULTI, bool YRULE = MULTI>
 __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
                                            const LaneSeg<T>& ls, const T* dW) {
   const T h = ls.h;
+  // with several segments a segment without a grid runs the plain estimator
+  constexpr bool kCv = CV != kCvNone;
+  const bool use_cv = kCv && (CV != kCvGrid || !MULTI || ls.grad != nullptr);
+  // The cell-record gather depends only on X_k: it is issued before the
+  // coefficients are evaluated, so its latency overlaps their arithmetic.
+  T gv[3] = {T(0), T(0), T(0)};
+  if (CV == kCvGrid && use_cv) {
+    if (D == 2) {
+      if (UseCells<T, 2>::value)
+        grid_cells_2d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1],
+                         PDD_DEBUG_BOUNDS ? a.err : nullptr);
+      else
+        grid_grad_2d<T>((const float2*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1],
+                        PDD_DEBUG_BOUNDS ? a.err : nullptr);
+    } else {
+      if (UseCells<T, 3>::value)
+        grid_cells_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
+                         gv[2], PDD_DEBUG_BOUNDS ? a.err : nullptr);
+      else
+        grid_grad_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
+                        gv[2], PDD_DEBUG_BOUNDS ? a.err : nullptr);
+    }
+  }
   Coef<T> o;
   P::template eval<T, CV == kCvExact>(s.x[0], s.x[1], s.x[2], o);
   T sdW[3];
@@ -168,24 +229,8 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
     sdW[1] = dW1;
   }
   sdW[2] = (D == 3) ? dW[2] : T(0);
-  // with several segments a segment without a grid runs the plain estimator
-  if (CV != kCvNone && (CV != kCvGrid || !MULTI || ls.grad != nullptr)) {
-    T gv[3] = {T(0), T(0), T(0)};
-    if (CV == kCvGrid) {
-      if (D == 2) {
-        if (UseCells<T, 2>::value)
-          grid_cells_2d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1]);
-        else
-          grid_grad_2d<T>((const float2*)ls.grad, ls.gn, s.x[0], s.x[1], gv[0], gv[1]);
-      } else {
-        if (UseCells<T, 3>::value)
-          grid_cells_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
-                           gv[2]);
-        else
-          grid_grad_3d<T>((const float4*)ls.grad, ls.gn, s.x[0], s.x[1], s.x[2], gv[0], gv[1],
-                          gv[2]);
-      }
-    } else {
+  if (use_cv) {
+    if (CV == kCvExact) {
       gv[0] = o.g0;
       gv[1] = o.g1;
       gv[2] = o.g2;
@@ -263,6 +308,9 @@ __device__ __forceinline__ void cache_flush(const PathArgs& a) {
       else hi = mid - 1;
     }
     const SegArgs& sg = a.seg[lo];
+    if (!PDD_IN_BOUNDS(a, slot >= sg.cache_base && slot - sg.cache_base < sg.n_nodes,
+                       kErrBoundsRecord))
+      continue;
     unsigned long long* g = sg.acc + (size_t)(slot - sg.cache_base) * kAccWords;
     if (q < 7) {
       if ((s[2 * q] | s[2 * q + 1]) != 0ull) atomic_add_u128(g + 2 * q, s[2 * q], s[2 * q + 1]);
@@ -281,7 +329,9 @@ __device__ __forceinline__ void cache_flush(const PathArgs& a) {
 template <class T>
 __device__ __forceinline__ void record_path(const PathArgs& a, const SegArgs& sg, uint32_t node,
                                             T phi, T psi, int k_steps, bool trunc) {
+  if (!PDD_IN_BOUNDS(a, node < sg.n_nodes, kErrBoundsRecord)) return;
   if (a.cache_nodes != 0) {
+    if (!PDD_IN_BOUNDS(a, sg.cache_base + node < a.cache_nodes, kErrBoundsRecord)) return;
     accumulate(a, s_cache + (size_t)(sg.cache_base + node) * kCacheStride,
                a.steps_total != nullptr ? s_cache + (size_t)a.cache_nodes * kCacheStride : nullptr,
                phi, psi, k_steps, trunc);
@@ -309,6 +359,7 @@ __device__ __forceinline__ void finish_path(const PathArgs& a, const PathState<T
   record_path(a, sg, s.node, phi, phi + xi, s.k, trunc);
   if (sg.emit_phi != nullptr) {
     const size_t i = (size_t)s.node * sg.emit_stride + s.path;
+    if (!PDD_IN_BOUNDS(a, i < sg.n_nodes * sg.emit_stride, kErrBoundsEmit)) return;
     sg.emit_phi[i] = (float)phi;
     sg.emit_xi[i] = (float)xi;
     sg.emit_steps[i] = s.k;
@@ -432,6 +483,8 @@ __device__ __forceinline__ void ring_exit(const PathArgs& a, const ExitRing<T, D
                                           bool trunc) {
   const unsigned m = __ballot_sync(kFull, done);
   if (m == 0u) return;
+  // never more than kRing parked: fewer than 32 are held before this iteration
+  if (!PDD_IN_BOUNDS(a, c.held + __popc(m) <= kRing, kErrBoundsRing)) return;
   if (done) {
     const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
     ring_put<T, D>(r, (c.head + __popc(m & lt)) & (kRing - 1), s, trunc);
@@ -616,7 +669,9 @@ __device__ __forceinline__ void pair_drain(const PathArgs& a, const PairRing<T>&
     const SegArgs& s1 = a.seg[1];
     record_path(a, s0, node, phif, phif + xif, kf, (tr & 1u) != 0u);
     record_path(a, s1, node, phif - phic, (phif + xif) - (phic + xic), kc, (tr & 2u) != 0u);
-    if (s0.emit_phi != nullptr) {
+    if (s0.emit_phi != nullptr &&
+        PDD_IN_BOUNDS(a, (size_t)node * s0.emit_stride + path < s0.n_nodes * s0.emit_stride,
+                      kErrBoundsEmit)) {
       const size_t i = (size_t)node * s0.emit_stride + path;
       s0.emit_phi[i] = (float)phif;
       s0.emit_xi[i] = (float)xif;
@@ -705,7 +760,11 @@ __global__ void __launch_bounds__(kMaxBlockThreads, 1) paths_coupled(
     // park finished pairs; drain 32 at a time with the whole warp
     const bool done = active && !af && !ac;
     const unsigned m = __ballot_sync(kFull, done);
-    if (m != 0u) {
+    // never more than kRing parked: fewer than 32 are held before this iteration
+    // (bounds-checked build: an over-full ring drops the pairs, never stalls)
+    if (m != 0u && !PDD_IN_BOUNDS(a, rc.held + __popc(m) <= kRing, kErrBoundsRing)) {
+      if (done) active = false;
+    } else if (m != 0u) {
       if (done) {
         const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
         const uint32_t q = (rc.head + __popc(m & lt)) & (kRing - 1);
@@ -766,11 +825,8 @@ cudaError_t launch_coupled(int kind, int cv, const PathArgs& a, int num_sms, cud
 // ---------------------------------------------------------------------------
 // Finalisation: one thread per node turns the exact sums into FP64 moments.
 // ---------------------------------------------------------------------------
-__global__ void finalize_nodes(const unsigned long long* __restrict__ acc, uint32_t n_nodes,
-                               double kappa, const __grid_constant__ StatPtrs out) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_nodes) return;
-  const unsigned long long* w = acc + (size_t)i * kAccWords;
+__device__ __forceinline__ void finalize_one(const unsigned long long* __restrict__ w,
+                                             uint32_t i, double kappa, const StatPtrs& out) {
   const double inv1 = 1.0 / kFxScale, inv2 = inv1 * inv1;
   const double n = (double)w[14];
   const double s_phi = s128_to_double(w[0], w[1]) * inv1;
@@ -780,8 +836,12 @@ __global__ void finalize_nodes(const unsigned long long* __restrict__ acc, uint3
   const double s_pp = s128_to_double(w[8], w[9]) * inv2;
   const double s_k = u128_to_double(w[10], w[11]);
   const double m_phi = s_phi / n, m_psi = s_psi / n;
-  const double v_phi = (s_phi2 - s_phi * m_phi) / (n - 1.0);
-  const double v_psi = (s_psi2 - s_psi * m_psi) / (n - 1.0);
+  // the exact sums' conversion to FP64 can leave a zero variance a rounding
+  // below zero; clamp it (n = 1 stays NaN: 0 / 0)
+  double v_phi = (s_phi2 - s_phi * m_phi) / (n - 1.0);
+  double v_psi = (s_psi2 - s_psi * m_psi) / (n - 1.0);
+  v_phi = v_phi < 0.0 ? 0.0 : v_phi;
+  v_psi = v_psi < 0.0 ? 0.0 : v_psi;
   const double c_pp = (s_pp - s_phi * m_psi) / (n - 1.0);  // Cov[phi, phi + xi]
   const double c_px = c_pp - v_phi;                         // Cov[phi, xi]
   const double v_xi = v_psi + v_phi - 2.0 * c_pp;           // V[xi]
@@ -799,6 +859,37 @@ __global__ void finalize_nodes(const unsigned long long* __restrict__ acc, uint3
   if (out.mean_steps) out.mean_steps[i] = s_k / n;
   if (out.n_paths) out.n_paths[i] = w[14];
   if (out.n_truncated) out.n_truncated[i] = w[15];
+}
+
+__global__ void finalize_nodes(const unsigned long long* __restrict__ acc, uint32_t n_nodes,
+                               double kappa, const __grid_constant__ StatPtrs out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nodes) return;
+  finalize_one(acc + (size_t)i * kAccWords, i, kappa, out);
+}
+
+// All levels of a launch in one kernel: thread t finalises record t of the
+// contiguous record array, whose level is the last one with base <= t.
+struct FinalizeLevels {
+  uint32_t n_levels;
+  uint32_t total;
+  uint32_t base[kMaxSegments + 1];  // first record of each level; base[n_levels] = total
+  double kappa[kMaxSegments];
+  StatPtrs out[kMaxSegments];
+};
+static_assert(sizeof(FinalizeLevels) < 32000, "kernel parameter size");
+
+__global__ void finalize_levels(const unsigned long long* __restrict__ acc,
+                                const __grid_constant__ FinalizeLevels f) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= f.total) return;
+  int lo = 0, hi = (int)f.n_levels - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (f.base[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  finalize_one(acc + (size_t)t * kAccWords, t - f.base[lo], f.kappa[lo], f.out[lo]);
 }
 
 // ---------------------------------------------------------------------------
@@ -955,6 +1046,31 @@ cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int
                  : launch_kind<double, false>(kind, cv, a, num_sms, st, blocks);
   return multi ? launch_kind<float, true>(kind, cv, a, num_sms, st, blocks)
                : launch_kind<float, false>(kind, cv, a, num_sms, st, blocks);
+}
+
+cudaError_t launch_finalize_levels(const unsigned long long* acc, int n_levels,
+                                   const uint32_t* node_base, const uint32_t* n_nodes,
+                                   const double* kappa, const StatPtrs* out, cudaStream_t st) {
+  if (n_levels < 1 || n_levels > kMaxSegments) return cudaErrorInvalidValue;
+  FinalizeLevels f{};
+  uint32_t total = 0;
+  int k = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    if (n_nodes[l] == 0) continue;
+    if (node_base[l] != total) return cudaErrorInvalidValue;  // records must be contiguous
+    f.base[k] = total;
+    f.kappa[k] = kappa[l];
+    f.out[k] = out[l];
+    total += n_nodes[l];
+    ++k;
+  }
+  if (k == 0) return cudaSuccess;
+  f.n_levels = (uint32_t)k;
+  f.base[k] = total;
+  f.total = total;
+  const unsigned threads = 128;
+  finalize_levels<<<(total + threads - 1) / threads, threads, 0, st>>>(acc, f);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(const unsigned long long* acc, uint32_t n_nodes, double kappa,

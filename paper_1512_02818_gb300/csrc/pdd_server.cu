@@ -15,6 +15,19 @@
 // finalisation and the copy of its results to page-locked host memory follow
 // on the same stream; the scheduler polls CUDA events (host side) and
 // pdd_poll hands the results over.  No device code waits on anything.
+//
+// Admission by predicted work: a request's work is predicted as n_nodes x
+// n_paths x the expected exit index of its (problem, dt), measured by a
+// pilot launch the first time the pair is seen and refined by every
+// completed request; with a deadline set, pdd_submit refuses a request whose
+// work, after the predicted remaining work of everything queued and running,
+// would not finish within the deadline at the measured rate (path-steps of
+// retired launches over the time they took).  Under the earliest-deadline
+// policy (every request has the same relative deadline, so it serves them in
+// submission order) the admitted work finishes in time as far as the
+// prediction holds, and no executed work is thrown away under overload;
+// under fair shares or shortest-first a request admitted earlier can be
+// slowed by later ones.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -108,6 +121,7 @@ struct Request {
   RState state = RState::kPending;
   int status = PDD_OK;
   uint64_t next_path = 0;  // paths per node already issued
+  uint64_t retired_paths = 0;  // paths per node whose launches have completed
   size_t dev_off = 0, dev_bytes = 0, host_off = 0, host_bytes = 0;
   bool has_mem = false;
   int inflight = 0;  // in-flight launches that reference this request
@@ -123,7 +137,20 @@ struct Launch {
   cudaEvent_t ev = nullptr;
   int stream = 0;
   std::vector<uint64_t> tickets;
+  std::vector<uint64_t> paths;  // paths per node of each ticket's slice
+  Clock::time_point t_issue;
 };
+
+// Expected exit index of the paths of one (problem, dt): a weighted mean over
+// the pilot's and the completed requests' paths.
+struct StepsEst {
+  double steps = 0.0;
+  double weight = 0.0;
+};
+
+constexpr int kPilotNodes = 128;        // nodes of a request the pilot samples
+constexpr uint64_t kPilotPaths = 64;    // paths per pilot node
+constexpr double kDefaultRate = 1e11;   // path-steps/s before any launch has retired
 
 }  // namespace
 
@@ -137,7 +164,15 @@ struct pdd_server {
   char* dev_arena = nullptr;
   char* host_arena = nullptr;  // page-locked results
   char* hdr = nullptr;         // per-launch header slots (cursor, err, trunc, steps): 2 x 256 B
-  unsigned long long* steps_host = nullptr;  // page-locked: path-steps of the last launch per stream
+  unsigned long long* hdr_host = nullptr;  // page-locked copies of the 2 headers (4 words each)
+  cudaStream_t pilot_stream = nullptr;
+  char* pilot_dev = nullptr;   // pilot scratch: header | records | coordinates | mean steps
+  double* pilot_host = nullptr;  // page-locked mean exit index of the pilot nodes
+  std::mutex pilot_mu;
+  std::map<std::pair<pdd_problem*, double>, StepsEst> steps_est;
+  double rate = 0.0;           // measured path-steps/s (0: not yet)
+  Clock::time_point last_retire;
+  bool busy_since_retire = false;
   Arena dmem, hmem;
   std::mutex mu;
   std::condition_variable cv_done, cv_work;
@@ -191,6 +226,100 @@ void finish_request(pdd_server* s, Request& r, RState state, int status) {
   else if (state == RState::kCancelled) s->st.cancelled++;
   else s->st.failed++;
   s->cv_done.notify_all();
+}
+
+// Predicted path-steps still to run for a queued or running request: the
+// paths whose launches have not completed yet.
+double remaining_work(const Request& r) {
+  if (r.state != RState::kPending && r.state != RState::kActive &&
+      r.state != RState::kFinishing)
+    return 0.0;
+  return (double)(r.n_paths - r.retired_paths) * (double)r.n_nodes * r.est_steps;
+}
+
+double backlog_work(pdd_server* s) {
+  double b = 0.0;
+  for (uint64_t t : s->pending) {
+    auto it = s->reqs.find(t);
+    if (it != s->reqs.end()) b += remaining_work(*it->second);
+  }
+  for (uint64_t t : s->active) {
+    auto it = s->reqs.find(t);
+    if (it != s->reqs.end()) b += remaining_work(*it->second);
+  }
+  return b;
+}
+
+double current_rate(const pdd_server* s) {
+  if (s->rate > 0.0) return s->rate;
+  return s->desc.rate_hint > 0.0 ? s->desc.rate_hint : kDefaultRate;
+}
+
+size_t pilot_bytes() {
+  return 256 + (size_t)kPilotNodes * kAccWords * 8 + 3 * align256(kPilotNodes * 4) +
+         align256(kPilotNodes * 8);
+}
+
+// Expected exit index at r.dt from a pilot launch: kPilotPaths plain paths
+// from each of up to kPilotNodes nodes of the request, on the server's pilot
+// stream (synchronous; it queues behind launches already on the device).
+int run_pilot(pdd_server* s, const Request& r, double* steps) {
+  std::lock_guard<std::mutex> lk(s->pilot_mu);
+  DeviceGuard guard(s->device);
+  const int dim = r.pv.dim;
+  const int64_t n = std::min<int64_t>(r.n_nodes, kPilotNodes);
+  char* hdr = s->pilot_dev;
+  unsigned long long* acc = (unsigned long long*)(hdr + 256);
+  char* coords = hdr + 256 + (size_t)kPilotNodes * kAccWords * 8;
+  double* mean_steps = (double*)(coords + 3 * align256(kPilotNodes * 4));
+  float sample[3][kPilotNodes];
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t src = n == r.n_nodes ? i : i * r.n_nodes / n;  // evenly spread
+    for (int j = 0; j < dim; ++j) sample[j][i] = r.coords[j][(size_t)src];
+  }
+  cudaStream_t st = s->pilot_stream;
+  cudaError_t e = cudaMemsetAsync(hdr, 0, 256 + (size_t)n * kAccWords * 8, st);
+  for (int j = 0; j < dim && e == cudaSuccess; ++j)
+    e = cudaMemcpyAsync(coords + j * align256(kPilotNodes * 4), sample[j], (size_t)n * 4,
+                        cudaMemcpyHostToDevice, st);
+  PathArgs pa{};
+  pa.cursor = (unsigned long long*)hdr;
+  pa.err = (unsigned*)(hdr + 8);
+  pa.trunc_total = (unsigned long long*)(hdr + 16);
+  pa.y_exp = r.pv.y_rule == PDD_Y_EXP;
+  pa.n_segs = 1;
+  SegArgs& sg = pa.seg[0];
+  sg.cx = (const float*)coords;
+  sg.cy = (const float*)(coords + align256(kPilotNodes * 4));
+  sg.cz = dim == 3 ? (const float*)(coords + 2 * align256(kPilotNodes * 4)) : sg.cx;
+  sg.total = (unsigned long long)n * kPilotPaths;
+  sg.n_paths = kPilotPaths;
+  sg.n_nodes = (unsigned long long)n;
+  sg.acc = acc;
+  sg.emit_stride = kPilotPaths;
+  sg.h = r.dt;
+  sg.sqrt_h = std::sqrt(r.dt);
+  sg.thr0 = (r.pv.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0) * sg.sqrt_h;
+  sg.key0 = 0x5eed1u;  // a stream of its own, apart from any request's
+  sg.key1 = 0xFFFFFFF0u;
+  sg.max_steps = r.max_steps;
+  pa.total = sg.total;
+  int blocks = 0;
+  if (e == cudaSuccess) e = launch_paths(r.pv.kind, r.pv.precision, 0, pa, s->num_sms, st, &blocks);
+  StatPtrs sp{};
+  sp.mean_steps = mean_steps;
+  if (e == cudaSuccess) e = launch_finalize(acc, (uint32_t)n, 1.0, sp, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->pilot_host, mean_steps, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error("pdd_submit: pilot launch: %s", cudaGetErrorString(e));
+    return PDD_ERR_CUDA;
+  }
+  double m = 0.0;
+  for (int64_t i = 0; i < n; ++i) m += s->pilot_host[i];
+  *steps = n > 0 ? m / (double)n : 0.0;
+  return PDD_OK;
 }
 
 // Admit pending requests while slots and arena room allow (FIFO, no overtaking).
@@ -268,11 +397,15 @@ bool issue_launch(pdd_server* s) {
   };
   const double quantum = (double)s->desc.quantum_path_steps;
   std::vector<uint64_t> take(batch.size(), 0);
-  if (s->desc.policy == PDD_SERVE_SHORTEST) {
-    std::stable_sort(batch.begin(), batch.end(), [&](const Request* x, const Request* y) {
-      return (double)(x->n_paths - x->next_path) * per_path_of(x) <
-             (double)(y->n_paths - y->next_path) * per_path_of(y);
-    });
+  if (s->desc.policy == PDD_SERVE_SHORTEST || s->desc.policy == PDD_SERVE_EARLIEST_DEADLINE) {
+    // shortest remaining work first; or, with one relative deadline for every
+    // request, earliest deadline first = submission order, which is the order
+    // of the running batch already
+    if (s->desc.policy == PDD_SERVE_SHORTEST)
+      std::stable_sort(batch.begin(), batch.end(), [&](const Request* x, const Request* y) {
+        return (double)(x->n_paths - x->next_path) * per_path_of(x) <
+               (double)(y->n_paths - y->next_path) * per_path_of(y);
+      });
     double budget = quantum;
     for (size_t i = 0; i < batch.size() && budget > 0.0; ++i) {
       const double pp = per_path_of(batch[i]);
@@ -351,17 +484,19 @@ bool issue_launch(pdd_server* s) {
     r->next_path += m;
     r->inflight += 1;
     L.tickets.push_back(r->ticket);
+    L.paths.push_back(m);
   }
   pa.n_segs = ns;
   pa.total = begin;
   int blocks = 0;
   if (e == cudaSuccess) e = launch_paths(pv.kind, pv.precision, cv, pa, s->num_sms, st, &blocks);
-  // the launch's executed path-steps, read when its event has completed; the
-  // slot is not reused before then (the next launch on this stream is issued
-  // after this one retires)
+  // the launch's header (error word, executed path-steps), read when its event
+  // has completed; the slot is not reused before then (the next launch on this
+  // stream is issued after this one retires)
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(s->steps_host + sidx, pa.steps_total, 8, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(s->hdr_host + 4 * sidx, hdr, 32, cudaMemcpyDeviceToHost, st);
   L.stream = sidx;
+  L.t_issue = Clock::now();
   s->st.launches++;
   // requests whose last slice is in this launch: finalise and copy out
   const cudaEvent_t prev = s->inflight.empty() ? nullptr : s->inflight.back().ev;
@@ -409,10 +544,34 @@ bool issue_launch(pdd_server* s) {
 void retire(pdd_server* s) {
   while (!s->inflight.empty() && cudaEventQuery(s->inflight.front().ev) == cudaSuccess) {
     Launch& L = s->inflight.front();
-    s->st.path_steps += (int64_t)s->steps_host[L.stream];
-    for (uint64_t t : L.tickets) {
-      auto it = s->reqs.find(t);
-      if (it != s->reqs.end()) it->second->inflight -= 1;
+    const unsigned long long* h = s->hdr_host + 4 * L.stream;
+    const double steps = (double)h[3];
+    s->st.path_steps += (int64_t)h[3];
+    const unsigned err = (unsigned)(h[1] & 0xFFFFFFFFull);
+    // measured rate: path-steps over the time since the GPU last became busy
+    // with this launch (the previous retirement, or this launch's issue)
+    const Clock::time_point now = Clock::now();
+    const Clock::time_point from =
+        s->busy_since_retire && s->last_retire > L.t_issue ? s->last_retire : L.t_issue;
+    const double secs = std::chrono::duration<double>(now - from).count();
+    if (steps >= 1e8 && secs > 0.0) {
+      const double sample = steps / secs;
+      s->rate = s->rate > 0.0 ? 0.7 * s->rate + 0.3 * sample : sample;
+    }
+    s->last_retire = now;
+    s->busy_since_retire = s->inflight.size() > 1;
+    const int fail_status = err != 0u ? error_word_status(err, "pdd server launch") : PDD_OK;
+    for (size_t k = 0; k < L.tickets.size(); ++k) {
+      auto it = s->reqs.find(L.tickets[k]);
+      if (it == s->reqs.end()) continue;
+      Request& r = *it->second;
+      r.inflight -= 1;
+      r.retired_paths += L.paths[k];
+      if (fail_status != PDD_OK &&
+          (r.state == RState::kActive || r.state == RState::kFinishing)) {
+        r.next_path = r.n_paths;
+        finish_request(s, r, RState::kFailed, fail_status);
+      }
     }
     cudaEventDestroy(L.ev);
     s->inflight.pop_front();
@@ -421,6 +580,17 @@ void retire(pdd_server* s) {
     Request& r = *s->reqs[s->active[i]];
     bool drop = false;
     if (r.state == RState::kFinishing && r.done && cudaEventQuery(r.done) == cudaSuccess) {
+      // exit indices of the completed request: goodput and the (problem, dt) estimate
+      const size_t n8 = align256((size_t)r.n_nodes * 8);
+      const double* ms = (const double*)(s->host_arena + r.host_off + 11 * n8);
+      double m = 0.0;
+      for (int64_t i = 0; i < r.n_nodes; ++i) m += ms[i];
+      m /= (double)r.n_nodes;
+      s->st.completed_path_steps += (int64_t)(m * (double)r.n_nodes * (double)r.n_paths);
+      StepsEst& est = s->steps_est[{r.prob, r.dt}];
+      const double w = (double)r.n_nodes * (double)r.n_paths;
+      est.steps = (est.steps * est.weight + m * w) / (est.weight + w);
+      est.weight += w;
       finish_request(s, r, RState::kDone, PDD_OK);
       drop = true;
     } else if ((r.state == RState::kCancelled || r.state == RState::kFailed) && r.inflight == 0 &&
@@ -482,8 +652,14 @@ int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** ou
   if (d.max_queue <= 0) d.max_queue = 256;
   if (d.quantum_path_steps <= 0) d.quantum_path_steps = 8000000000ll;
   if (d.device_arena_bytes == 0) d.device_arena_bytes = (size_t)256 << 20;
-  if (d.policy != PDD_SERVE_FAIR && d.policy != PDD_SERVE_SHORTEST) {
-    set_error("pdd_server_create: policy %d is not PDD_SERVE_FAIR or PDD_SERVE_SHORTEST", d.policy);
+  if (!(d.deadline_s >= 0.0) || !(d.rate_hint >= 0.0)) {
+    set_error("pdd_server_create: deadline_s and rate_hint must be >= 0");
+    return PDD_ERR_INVALID;
+  }
+  if (d.policy != PDD_SERVE_FAIR && d.policy != PDD_SERVE_SHORTEST &&
+      d.policy != PDD_SERVE_EARLIEST_DEADLINE) {
+    set_error("pdd_server_create: policy %d is not PDD_SERVE_FAIR, PDD_SERVE_SHORTEST or "
+              "PDD_SERVE_EARLIEST_DEADLINE", d.policy);
     return PDD_ERR_INVALID;
   }
   auto s = std::make_unique<pdd_server>();
@@ -501,19 +677,25 @@ int pdd_server_create(pdd_ctx* ctx, const pdd_server_desc* desc, pdd_server** ou
   cudaError_t e = cudaMalloc((void**)&s->dev_arena, d.device_arena_bytes);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s->host_arena, host_bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&s->hdr, 512);
-  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->steps_host, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->hdr_host, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&s->pilot_dev, pilot_bytes());
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&s->pilot_host, kPilotNodes * sizeof(double));
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     e = cudaStreamCreateWithFlags(&s->stream[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->pilot_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     set_error("pdd_server_create: %s", cudaGetErrorString(e));
     if (s->dev_arena) cudaFree(s->dev_arena);
     if (s->host_arena) cudaFreeHost(s->host_arena);
     if (s->hdr) cudaFree(s->hdr);
-    if (s->steps_host) cudaFreeHost(s->steps_host);
+    if (s->hdr_host) cudaFreeHost(s->hdr_host);
+    if (s->pilot_dev) cudaFree(s->pilot_dev);
+    if (s->pilot_host) cudaFreeHost(s->pilot_host);
     for (auto& x : s->stream)
       if (x) cudaStreamDestroy(x);
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->pilot_stream) cudaStreamDestroy(s->pilot_stream);
     return e == cudaErrorMemoryAllocation ? PDD_ERR_NOMEM : PDD_ERR_CUDA;
   }
   s->dmem.reset(d.device_arena_bytes);
@@ -579,7 +761,6 @@ int pdd_submit(pdd_server* s, pdd_problem* p, const pdd_estimate_args* a, uint64
   int64_t ms = r->pv.max_steps;
   if (ms <= 0) ms = (int64_t)std::min(2.0e9, std::ceil(100.0 / a->dt));
   r->max_steps = (int)std::min<int64_t>(ms, 2000000000ll);
-  r->est_steps = (dim == 3 ? 0.05 : 0.12) / a->dt;
   // copy the inputs now: the caller may reuse its buffers on return
   for (int j = 0; j < dim; ++j) {
     r->coords[j].resize((size_t)a->n_nodes);
@@ -596,12 +777,42 @@ int pdd_submit(pdd_server* s, pdd_problem* p, const pdd_estimate_args* a, uint64
       std::memcpy(r->coords[j].data(), a->coords[j], (size_t)a->n_nodes * 4);
     }
   }
+  // expected exit index of this (problem, dt): cached, else a pilot launch
+  double est = 0.0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->steps_est.find({p, a->dt});
+    if (it != s->steps_est.end()) est = it->second.steps;
+  }
+  if (est <= 0.0 && r->n_nodes > 0) {
+    const int rc = run_pilot(s, *r, &est);
+    if (rc != PDD_OK) return rc;
+    std::lock_guard<std::mutex> lk(s->mu);
+    StepsEst& e = s->steps_est[{p, a->dt}];
+    if (e.weight == 0.0) {
+      e.steps = est;
+      e.weight = (double)std::min<int64_t>(r->n_nodes, kPilotNodes) * (double)kPilotPaths;
+    }
+  }
+  r->est_steps = std::max(1.0, est);
   std::lock_guard<std::mutex> lk(s->mu);
   s->st.submitted++;
   if ((int64_t)s->pending.size() >= s->desc.max_queue) {
     s->st.rejected_busy++;
     set_error("pdd_submit: admission queue full (%d requests)", s->desc.max_queue);
     return PDD_ERR_BUSY;
+  }
+  if (s->desc.deadline_s > 0.0) {
+    const double work = (double)r->n_nodes * (double)r->n_paths * r->est_steps;
+    const double backlog = backlog_work(s);
+    const double rate = current_rate(s);
+    if ((backlog + work) / rate > s->desc.deadline_s) {
+      s->st.rejected_deadline++;
+      set_error("pdd_submit: predicted %.3g path-steps after a backlog of %.3g do not finish "
+                "within the %.3g s deadline at %.3g path-steps/s",
+                work, backlog, s->desc.deadline_s, rate);
+      return PDD_ERR_DEADLINE;
+    }
   }
   auto git = s->group_ids.find(p);
   int gid = (int)s->group_ids.size() * 3;
@@ -710,6 +921,8 @@ int pdd_server_get_stats(pdd_server* s, pdd_server_stats* out) {
   *out = s->st;
   out->pending = (int64_t)s->pending.size();
   out->active = (int64_t)s->active.size();
+  out->backlog_path_steps = (int64_t)backlog_work(s);
+  out->rate_path_steps_per_s = (int64_t)current_rate(s);
   return PDD_OK;
 }
 
@@ -742,6 +955,7 @@ void pdd_server_destroy(pdd_server* s) {
   DeviceGuard guard(s->device);
   for (auto& x : s->stream) cudaStreamSynchronize(x);
   cudaStreamSynchronize(s->copy_stream);
+  cudaStreamSynchronize(s->pilot_stream);
   for (auto& kv : s->reqs) {
     if (kv.second->ready) cudaEventDestroy(kv.second->ready);
     if (kv.second->done) cudaEventDestroy(kv.second->done);
@@ -751,9 +965,12 @@ void pdd_server_destroy(pdd_server* s) {
   cudaFree(s->dev_arena);
   cudaFreeHost(s->host_arena);
   cudaFree(s->hdr);
-  cudaFreeHost(s->steps_host);
+  cudaFreeHost(s->hdr_host);
+  cudaFree(s->pilot_dev);
+  cudaFreeHost(s->pilot_host);
   for (auto& x : s->stream) cudaStreamDestroy(x);
   cudaStreamDestroy(s->copy_stream);
+  cudaStreamDestroy(s->pilot_stream);
   delete s;
 }
 

@@ -16,11 +16,14 @@ import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpdd.so")
+# the bounds-checked build of the same library (build.build(bounds=True))
+LIB_BOUNDS_PATH = os.path.join(HERE, "libpdd_bounds.so")
 
 # ---- constants mirrored from include/pdd.h --------------------------------
 PDD_OK, PDD_ERR_INVALID, PDD_ERR_NOMEM, PDD_ERR_CUDA = 0, -1, -2, -3
 PDD_ERR_TIMEOUT, PDD_ERR_BUSY, PDD_ERR_NOT_READY, PDD_ERR_CANCELLED = -4, -5, -6, -7
 PDD_ERR_OVERFLOW, PDD_WARN_TRUNCATED, PDD_WARN_NOT_CONVERGED = -8, 1, 2
+PDD_ERR_BOUNDS, PDD_ERR_DEADLINE = -9, -10
 PDD_PROBLEM_CFG0_2D, PDD_PROBLEM_ANISO_2D, PDD_PROBLEM_CUBE_3D, PDD_PROBLEM_HARMONIC_2D = 0, 1, 2, 3
 PDD_PROBLEM_PAPER_EX_2D = 4
 PDD_EXIT_GOBET_MENOZZI, PDD_EXIT_NAIVE = 0, 1
@@ -96,10 +99,11 @@ class ScheduleArgs(ctypes.Structure):
 class ServerDesc(ctypes.Structure):
     _fields_ = [("max_active", ctypes.c_int32), ("max_queue", ctypes.c_int32),
                 ("quantum_path_steps", ctypes.c_int64), ("device_arena_bytes", ctypes.c_size_t),
-                ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("policy", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("deadline_s", ctypes.c_double), ("rate_hint", ctypes.c_double)]
 
 
-PDD_SERVE_FAIR, PDD_SERVE_SHORTEST = 0, 1
+PDD_SERVE_FAIR, PDD_SERVE_SHORTEST, PDD_SERVE_EARLIEST_DEADLINE = 0, 1, 2
 
 
 class MlmcArgs(ctypes.Structure):
@@ -125,7 +129,8 @@ class MlmcOut(ctypes.Structure):
 
 SERVER_STAT_FIELDS = ["submitted", "admitted", "rejected_busy", "rejected_invalid",
                       "rejected_nomem", "completed", "cancelled", "failed", "launches", "pending",
-                      "active", "path_steps"]
+                      "active", "path_steps", "rejected_deadline", "completed_path_steps",
+                      "backlog_path_steps", "rate_path_steps_per_s"]
 
 
 class ServerStats(ctypes.Structure):
@@ -172,6 +177,13 @@ _SIGS = [
                                          ctypes.POINTER(FitOut)]),
     ("pdd_schedule", ctypes.c_int, [ctypes.POINTER(ScheduleArgs), ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("pdd_debug_bounds_selftest", ctypes.c_int, [ctypes.POINTER(ctypes.c_uint32)]),
+    ("pdd_balanced_plan", ctypes.c_int, [ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]),
+    ("pdd_schedule_predict", ctypes.c_int, [ctypes.POINTER(ScheduleArgs), ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]),
     ("pdd_estimate_coupled", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
                                             ctypes.POINTER(NodeStats), ctypes.POINTER(NodeStats)]),
     ("pdd_accumulate_coupled", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(EstimateArgs),
@@ -218,6 +230,14 @@ def lib():
                 fn.argtypes = args
             _lib = l
         return _lib
+
+
+def bounds_selftest() -> int:
+    """Error word of the bounds-check self-test (62 in the bounds-checked
+    build, 0 in the release build)."""
+    bits = ctypes.c_uint32(0)
+    _check(lib().pdd_debug_bounds_selftest(ctypes.byref(bits)))
+    return bits.value
 
 
 def _check(status: int) -> int:
@@ -349,6 +369,35 @@ def pdd_schedule(K, beta, alpha, V_phi, V_psi, rho, delta: float, kappa: float, 
     return a[: J + 1].copy(), sp[:n_sp].copy()
 
 
+def pdd_balanced_plan(a: float, beta, var, q: float = 2.0, delta: float = 1.0,
+                      h_min: float = 1e-7, h_max: float = 0.1, n_min: int = 2,
+                      n_max: int = (1 << 32) - 1):
+    """Balanced time step and path count per node (eq. F:N_y_h): returns
+    (h, n_paths) numpy arrays."""
+    import numpy as np
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    v = np.ascontiguousarray(var, dtype=np.float64)
+    h = np.zeros(b.size)
+    n = np.zeros(b.size, dtype=np.int64)
+    _check(lib().pdd_balanced_plan(b.size, a, q, delta, b.ctypes.data, v.ctypes.data, h_min,
+                                   h_max, n_min, n_max, h.ctypes.data, n.ctypes.data))
+    return h, n
+
+
+def pdd_schedule_predict(K, beta, alpha, V_phi, V_psi, rho, delta: float, a: float, aj: float):
+    """Per-node predicted rho^2[phi_h, xi_h] and path-step cost of the level at
+    tolerance aj using the control variate of the level at tolerance a
+    (a <= 0: plain level); returns (rho2, cost)."""
+    import numpy as np
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (K, beta, alpha, V_phi, V_psi, rho)]
+    args = ScheduleArgs(arrs[0].size, *[x.ctypes.data for x in arrs], delta, 1.0, aj, 1.5)
+    rho2 = np.zeros(arrs[0].size)
+    cost = np.zeros(arrs[0].size)
+    _check(lib().pdd_schedule_predict(ctypes.byref(args), a, aj, rho2.ctypes.data,
+                                      cost.ctypes.data))
+    return rho2, cost
+
+
 def pdd_estimate_coupled(problem: int, args: EstimateArgs, out_fine: NodeStats,
                          out_diff: NodeStats) -> int:
     return _check(lib().pdd_estimate_coupled(problem, ctypes.byref(args), ctypes.byref(out_fine),
@@ -456,7 +505,15 @@ class Context:
         self.stream = stream if stream is not None else torch.cuda.Stream(device)
         if self.stream.cuda_stream == 0:
             raise ValueError("pass a non-default stream (handle 0 means 'library-owned')")
+        self._lib = lib()
         self.handle = pdd_ctx_create(device, self.stream.cuda_stream, mem_budget)
+        # Handles of the servers and problems still open on this context, held
+        # here and by those objects (a plain shared dict, not weak references,
+        # which the garbage collector clears before it runs the finalisers of a
+        # reference cycle): close() destroys what is still open first, and a
+        # later close() of such an object is a no-op.  Each entry keeps the
+        # library the object was created with.
+        self._owned = {"servers": {}, "problems": {}}
 
     def set_stream(self, stream) -> None:
         pdd_ctx_set_stream(self.handle, stream.cuda_stream)
@@ -495,7 +552,12 @@ class Context:
 
     def close(self) -> None:
         if self.handle:
-            pdd_ctx_destroy(self.handle)
+            for kind, fn in (("servers", "pdd_server_destroy"),
+                             ("problems", "pdd_destroy_problem")):
+                for h, l in list(self._owned[kind].items()):
+                    getattr(l, fn)(h)
+                self._owned[kind].clear()
+            self._lib.pdd_ctx_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -503,6 +565,13 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def _close_owned(owned: dict, handle, fn: str) -> None:
+    """Destroy `handle` unless its context already did (see Context)."""
+    l = owned.pop(handle, None)
+    if l is not None:
+        getattr(l, fn)(handle)
 
 
 class Problem:
@@ -516,6 +585,8 @@ class Problem:
         self.precision = precision
         self.handle = pdd_create_problem(ctx.handle, ProblemDesc(kind, exit_rule, y_rule,
                                                                  precision, max_steps))
+        self._owned = ctx._owned["problems"]
+        self._owned[self.handle] = ctx._lib
 
     def set_control_grid(self, grid_id: int, data, kind: int = PDD_GRID_VALUES) -> None:
         """data: numpy array or torch tensor (float32/float64, host or CUDA)
@@ -736,7 +807,7 @@ class Problem:
 
     def close(self) -> None:
         if self.handle:
-            pdd_destroy_problem(self.handle)
+            _close_owned(self._owned, self.handle, "pdd_destroy_problem")
             self.handle = None
 
     def __del__(self):
@@ -751,11 +822,15 @@ class Server:
 
     def __init__(self, ctx: Context, max_active: int = 0, max_queue: int = 0,
                  quantum_path_steps: int = 0, device_arena_bytes: int = 0,
-                 policy: int = PDD_SERVE_FAIR):
+                 policy: int = PDD_SERVE_FAIR, deadline_s: float = 0.0,
+                 rate_hint: float = 0.0):
         self.ctx = ctx
         self.handle = pdd_server_create(ctx.handle, ServerDesc(max_active, max_queue,
                                                                quantum_path_steps,
-                                                               device_arena_bytes, policy, 0))
+                                                               device_arena_bytes, policy, 0,
+                                                               deadline_s, rate_hint))
+        self._owned = ctx._owned["servers"]
+        self._owned[self.handle] = ctx._lib
 
     def submit(self, problem: Problem, nodes, n_paths: int, dt: float,
                grid_id: int = PDD_CV_NONE, seed: int = 1234, stream_tag: int = 0,
@@ -802,7 +877,7 @@ class Server:
 
     def close(self) -> None:
         if self.handle:
-            pdd_server_destroy(self.handle)
+            _close_owned(self._owned, self.handle, "pdd_server_destroy")
             self.handle = None
 
     def __del__(self):

@@ -242,3 +242,91 @@ def test_shortest_first_policy(env):
     srv.close()
     with pytest.raises(pdd.PddError):
         pdd.Server(ctx, policy=7)
+
+
+def test_deadline_admission_and_goodput(env):
+    """Admission by predicted work: with a deadline, a request whose predicted
+    path-steps cannot finish in time is refused at once (PDD_ERR_DEADLINE,
+    counted apart); admitted requests complete, so the completed path-steps
+    are the executed ones (goodput 1) and the results still equal the
+    requests run alone."""
+    torch, pdd, ctx, prob = env
+    srv = pdd.Server(ctx, max_active=16, max_queue=64, deadline_s=2.0, rate_hint=1e11)
+    rng = np.random.default_rng(17)
+    big = W.random_interface_nodes(rng, 4096)
+    # ~4096 x 1e6 x 1,200 path-steps: hours of work, far beyond 2 s
+    with pytest.raises(pdd.PddError) as e:
+        srv.submit(prob, big, 1_000_000, 1e-4, grid_id=1, stream_tag=7)
+    assert e.value.status == pdd.PDD_ERR_DEADLINE
+    small = _requests(seed=5, count=6)
+    tickets = [srv.submit(prob, r["nodes"], r["n_paths"], r["dt"], grid_id=r["grid_id"],
+                          seed=r["seed"], stream_tag=r["stream_tag"]) for r in small]
+    for t, r in zip(tickets, small):
+        st, res = _wait(srv, t, len(r["nodes"]))
+        assert st == pdd.PDD_OK
+        _same(pdd, res, _alone(prob, r))
+    s = srv.stats()
+    assert s["rejected_deadline"] == 1 and s["rejected_busy"] == 0
+    assert s["completed"] == len(small)
+    assert s["completed_path_steps"] > 0
+    assert abs(s["completed_path_steps"] - s["path_steps"]) <= 0.01 * s["path_steps"]
+    assert s["backlog_path_steps"] == 0 and s["rate_path_steps_per_s"] > 0
+    srv.close()
+
+
+def test_backlog_refusal(env):
+    """The deadline counts the queued and running work: a request that fits
+    alone is refused while a similar one, just admitted, is still running."""
+    torch, pdd, ctx, prob = env
+    srv = pdd.Server(ctx, max_active=4, max_queue=64, deadline_s=0.5, rate_hint=1e11)
+    nodes = W.workload_nodes("c1")
+    # ~256 x 1.3e5 x 1,100 = 3.7e10 path-steps: predicted 0.37 s at the assumed
+    # rate (the first call also runs the exit-time pilot of this time step)
+    t1 = srv.submit(prob, nodes, 130_000, 1e-4, grid_id=1, stream_tag=301)
+    with pytest.raises(pdd.PddError) as e:  # submitted at once, behind the first
+        srv.submit(prob, nodes, 130_000, 1e-4, grid_id=1, stream_tag=302)
+    assert e.value.status == pdd.PDD_ERR_DEADLINE
+    assert b"deadline" in pdd.lib().pdd_last_error()
+    st, _ = _wait(srv, t1, len(nodes))
+    assert st == pdd.PDD_OK
+    s = srv.stats()
+    assert s["rejected_deadline"] == 1 and s["completed"] == 1
+    # with the first one done, the same request fits again
+    t3 = srv.submit(prob, nodes, 130_000, 1e-4, grid_id=1, stream_tag=303)
+    st, _ = _wait(srv, t3, len(nodes))
+    assert st == pdd.PDD_OK
+    srv.close()
+
+
+def test_earliest_deadline_bounds_latency(env):
+    """Earliest-deadline policy with a deadline: under a burst far above
+    capacity the admitted requests are served in submission order and each
+    completes within the deadline (with slack for the predicted rate), the
+    rest is refused at once, and no executed work is thrown away."""
+    torch, pdd, ctx, prob = env
+    deadline = 1.0
+    srv = pdd.Server(ctx, max_active=32, max_queue=64, deadline_s=deadline,
+                     policy=pdd.PDD_SERVE_EARLIEST_DEADLINE)
+    nodes = W.workload_nodes("c1")
+    # prime the (problem, dt) estimate and the measured rate with one request
+    t = srv.submit(prob, nodes, 20_000, 1e-4, grid_id=1, stream_tag=500)
+    assert _wait(srv, t, len(nodes))[0] == pdd.PDD_OK
+    admitted, refused = {}, 0
+    for i in range(40):  # each ~5.6e9 path-steps: ~25-40 ms of GPU work
+        try:
+            tk = srv.submit(prob, nodes, 20_000, 1e-4, grid_id=1, stream_tag=501 + i)
+            admitted[tk] = time.perf_counter()
+        except pdd.PddError as e:
+            assert e.status == pdd.PDD_ERR_DEADLINE
+            refused += 1
+    assert admitted and refused
+    lat = []
+    for tk, t0 in admitted.items():
+        st, _ = _wait(srv, tk, len(nodes))
+        assert st == pdd.PDD_OK
+        lat.append(time.perf_counter() - t0)
+    assert max(lat) <= 2.0 * deadline, max(lat)
+    s = srv.stats()
+    assert s["rejected_deadline"] == refused
+    assert abs(s["completed_path_steps"] - s["path_steps"]) <= 0.01 * s["path_steps"]
+    srv.close()
