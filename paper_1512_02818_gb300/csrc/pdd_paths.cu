@@ -70,19 +70,6 @@ struct UseCells {
       sizeof(T) == 4 && ((D == 2 && PDD_CELLS_2D) || (D == 3 && PDD_CELLS_3D));
 };
 
-// Order of a launch's flat path index inside a segment: path-major (the
-// default: g = path * n_nodes + node, so the paths in flight belong to many
-// nodes) or node-major (g = node * n_paths + path: the paths in flight start
-// from a few nodes).  Build experiment: -DPDD_NODE_MAJOR_3D=1 makes 3D
-// launches node-major.
-#ifndef PDD_NODE_MAJOR_3D
-#define PDD_NODE_MAJOR_3D 0
-#endif
-template <int D>
-struct NodeMajor {
-  static constexpr bool value = D == 3 && PDD_NODE_MAJOR_3D;
-};
-
 template <class T>
 struct LaneSeg {
   T h, sqh, thr0;
@@ -129,18 +116,7 @@ __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long
     if (MULTI) load_seg<T, D>(a.seg[0], ls);
     return;
   }
-  if (NodeMajor<D>::value) {  // consecutive indices: consecutive paths of one node
-    if (sg.total <= 0xFFFFFFFFull) {
-      const uint32_t gg = (uint32_t)li, np = (uint32_t)sg.n_paths;
-      const uint32_t nd = gg / np;
-      s.node = nd;
-      s.path = sg.path_off + (gg - nd * np);
-    } else {
-      const unsigned long long nd = li / sg.n_paths;
-      s.node = (uint32_t)nd;
-      s.path = sg.path_off + (uint32_t)(li - nd * sg.n_paths);
-    }
-  } else if (sg.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
+  if (sg.total <= 0xFFFFFFFFull) {  // 32-bit division when the index space allows
     const uint32_t gg = (uint32_t)li, nn = (uint32_t)sg.n_nodes;
     const uint32_t p = gg / nn;
     s.node = gg - p * nn;
@@ -506,8 +482,13 @@ __device__ __forceinline__ void init_lane(const PathArgs& a, PathState<T>& s, La
   load_seg<T, D>(a.seg[0], ls);
 }
 
+// The segment-table build keeps per-lane segment parameters in registers; at
+// 65 registers a 512-thread block rounds up to 72 per thread and only one
+// block fits an SM, so it is capped at 64 (two blocks), which measured faster
+// than the uncapped build.
 template <class P, class T, int CV, bool MULTI>
-__global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_2D)
+__global__ void __launch_bounds__(kMaxBlockThreads, (MULTI && sizeof(T) == 4) ? 2
+                                                                               : PDD_MIN_BLOCKS_2D)
     paths_2d(const __grid_constant__ PathArgs a) {
   PathState<T> s;
   LaneSeg<T> ls;

@@ -170,7 +170,8 @@ struct pdd_server {
   double* pilot_host = nullptr;  // page-locked mean exit index of the pilot nodes
   std::mutex pilot_mu;
   std::map<std::pair<pdd_problem*, double>, StepsEst> steps_est;
-  double rate = 0.0;           // measured path-steps/s (0: not yet)
+  double busy_steps = 0.0;     // path-steps of all retired launches
+  double busy_s = 0.0;         // time the GPU was busy with them
   Clock::time_point last_retire;
   bool busy_since_retire = false;
   Arena dmem, hmem;
@@ -250,8 +251,11 @@ double backlog_work(pdd_server* s) {
   return b;
 }
 
+// Path-steps per second of GPU-busy time over every retired launch (launch
+// overheads and the drain of small launches included), once 0.2 s of busy
+// time has been seen; the hint (or 1e11) before.
 double current_rate(const pdd_server* s) {
-  if (s->rate > 0.0) return s->rate;
+  if (s->busy_s >= 0.2 && s->busy_steps > 0.0) return s->busy_steps / s->busy_s;
   return s->desc.rate_hint > 0.0 ? s->desc.rate_hint : kDefaultRate;
 }
 
@@ -548,15 +552,15 @@ void retire(pdd_server* s) {
     const double steps = (double)h[3];
     s->st.path_steps += (int64_t)h[3];
     const unsigned err = (unsigned)(h[1] & 0xFFFFFFFFull);
-    // measured rate: path-steps over the time since the GPU last became busy
-    // with this launch (the previous retirement, or this launch's issue)
+    // measured rate: this launch's path-steps over the time since the GPU last
+    // became busy with it (the previous retirement, or this launch's issue)
     const Clock::time_point now = Clock::now();
     const Clock::time_point from =
         s->busy_since_retire && s->last_retire > L.t_issue ? s->last_retire : L.t_issue;
     const double secs = std::chrono::duration<double>(now - from).count();
-    if (steps >= 1e8 && secs > 0.0) {
-      const double sample = steps / secs;
-      s->rate = s->rate > 0.0 ? 0.7 * s->rate + 0.3 * sample : sample;
+    if (secs > 0.0) {
+      s->busy_steps += steps;
+      s->busy_s += secs;
     }
     s->last_retire = now;
     s->busy_since_retire = s->inflight.size() > 1;
