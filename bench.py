@@ -54,6 +54,10 @@ ALGO_INSTR = {"plain": 111.2, "cv": 140.1}
 # pass) from the same full-size capture; None whenever the kernel has changed
 # since that capture.
 NCU_TRAFFIC_BYTES = 1461248
+# Thread-instructions per path-step of the 3D control-variate kernel over the
+# full-size cascade launch (ncu smsp__thread_inst_executed.sum over its path-
+# steps, profiles/paths_3d_c2_cascade.md; the planning estimate was 190).
+INSTR_3D = 228.3
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
@@ -270,7 +274,8 @@ def fixed_rmse_runs(torch, pdd, prob, dev, nodes_np, res_np, passes, rank, targe
     most target / sqrt(2) (the balanced choice of eq. F:N_y_h; the rest of the
     budget is the bias).  The nodes are sorted by N_i and split into up to 128
     groups, each run as one level of a single pdd_estimate_levels call with
-    the group's largest N_i and a stream of its own.  The call (device-resident
+    the group's largest N_i and a stream of its own, the groups with the
+    longest expected paths (exit indices of the timed step) first.  The call (device-resident
     inputs and outputs, synchronous) is timed on the host clock, after a
     1-path-per-node call of the same levels loaded the kernel.  The achieved
     RMSE is against the exact solution over all nodes, bias included."""
@@ -285,8 +290,13 @@ def fixed_rmse_runs(torch, pdd, prob, dev, nodes_np, res_np, passes, rank, targe
         need = np.maximum(2, np.ceil(var / (target * target / 2.0))).astype(np.int64)
         groups = [g for g in np.array_split(np.argsort(need, kind="stable"), min(128, n))
                   if g.size]
+        # launch order: the groups with the longest expected paths first (their
+        # segments' paths start in the launch's first wave instead of joining a
+        # late wave and lengthening its tail); each group keeps its own stream
+        order = sorted(range(len(groups)), key=lambda gi: -float(r["mean_steps"][groups[gi]].max()))
         levels = []
-        for gi, idx in enumerate(groups):
+        for gi in order:
+            idx = groups[gi]
             cols = [torch.from_numpy(np.ascontiguousarray(nodes_np[idx, j])).to(dev)
                     for j in range(2)]
             levels.append((idx, cols, int(need[idx].max()),
@@ -622,13 +632,14 @@ def run_c2(args):
             "levels": per_level, "graph_captures": ctx.graph_count(),
             "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
             "roofline": {"bound": "alu", "unit": "T thread-instr/s",
-                         "achieved": 190.0 * value / 1e12,
+                         "achieved": INSTR_3D * value / 1e12,
                          "peak": torch.cuda.get_device_properties(0).multi_processor_count
                          * 4 * 32 * 2.070e9 / 1e12,
-                         "algorithmic": "190 thread-instr per 3D control-variate path-step",
-                         "second_limit": "L1 data pipe: 79 % of its peak in the ncu capture of "
+                         "algorithmic": f"{INSTR_3D} thread-instr per 3D control-variate "
+                                        "path-step (ncu, executed, full-size cascade launch)",
+                         "second_limit": "L1 data pipe: 78 % of its peak in the ncu capture of "
                                          "the profiling case (two 256-bit cell-record gathers "
-                                         "per step), issue 74 %"}}
+                                         "per step), issue 75 %"}}
     line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     prob.close()
     ctx.close()
