@@ -359,9 +359,10 @@ def fit_constants(kind, nodes, n_paths, h_min, h_max, n_h, delta=1.0, q=2.0, see
         out["rho_phi_psi"][i] = out["cov_phi_psi"][i] / np.sqrt(out["V_phi"][i] * out["V_psi"][i])
         # nodal cost constant of eq. F:Pointwise_cost
         out["K"][i] = 4 * q * q * out["E_tau"][i] * (2 * abs(out["beta"][i])) ** (1 / delta)
-        # every path left at k = 0 at some h (zero sample variance: the node is
-        # inside the shrinkage layer there): the fitted model does not hold
-        if np.any(~(cloud[i, :, 2] > 0)):
+        # every path left at k = 0 at some h (mean exit time exactly 0, phi
+        # deterministic: the node is inside the shrinkage layer there): the
+        # fitted model does not hold
+        if np.any(~(cloud[i, :, 3] > 0)):
             for k in out:
                 out[k][i] = np.nan
     out["cloud"] = cloud

@@ -156,11 +156,12 @@ extern "C" int pdd_fit_constants(pdd_problem* p, const pdd_fit_args* a, pdd_fit_
   auto stat = [&](size_t j, int f, size_t i) { return hstat[(j * kF + f) * n + i]; };
   for (size_t i = 0; i < n; ++i) {
     // A node whose paths all leave at k = 0 at some time step of the cloud
-    // (zero sample variance: it lies inside the shrinkage layer c0 sqrt(h) of
-    // the boundary there) is outside the model E[eta_h] = E[eta_0] + B h^delta
-    // the fits assume: its constants are NaN and the schedule leaves it out.
+    // (mean exit index exactly 0, so phi is deterministic there: the node lies
+    // inside the shrinkage layer c0 sqrt(h) of the boundary) is outside the
+    // model E[eta_h] = E[eta_0] + B h^delta the fits assume: its constants are
+    // NaN and the schedule leaves it out.
     bool degenerate = false;
-    for (size_t j = 0; j < M; ++j) degenerate |= !(stat(j, 1, i) > 0.0);
+    for (size_t j = 0; j < M; ++j) degenerate |= !(stat(j, 2, i) > 0.0);
     if (degenerate) {
       double* const outs[9] = {out->E_phi, out->beta, out->V_phi, out->alpha, out->E_tau,
                                out->K, out->cov_phi_psi, out->V_psi, out->rho_phi_psi};

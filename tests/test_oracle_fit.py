@@ -60,3 +60,17 @@ def test_fit_recovers_solution_and_exit_time(oracle_mod):
     assert r["rho_phi_psi"][0] < -0.98
     assert r["K"][0] > 0
     assert np.allclose(c[:, 0], oracle_mod.h_cloud(2e-3, 1e-2, 5))
+
+
+def test_node_inside_shrinkage_layer_is_not_fitted(oracle_mod):
+    """A node within c0 sqrt(h_max) of the boundary has every path leave at
+    k = 0 at the coarse end of the cloud (mean exit time 0, phi deterministic): the
+    fitted model does not hold and its constants are NaN, while a node away
+    from the boundary in the same call is fitted."""
+    nodes = np.array([[0.01, 0.5], [0.5, 0.3]], dtype=np.float32)
+    r = oracle_mod.fit_constants(0, nodes, 200, 2e-3, 1e-2, 4, delta=1.0)
+    c = r["cloud"][0]
+    assert c[0, 3] == 0.0  # h = 1e-2: 0.5826 * 0.1 > 0.01, every path stops at once
+    assert c[0, 2] < 1e-20  # phi is deterministic there
+    for k in ("E_phi", "beta", "V_phi", "K", "E_tau"):
+        assert np.isnan(r[k][0]) and np.isfinite(r[k][1]), k

@@ -129,3 +129,30 @@ def test_cascade_plan_groups_partition_the_nodes():
             assert x.max() <= y.min()
         assert np.all((lv["h"] >= 1e-5) & (lv["h"] <= 1e-2))
         assert np.all(lv["pred_path_steps"] > 0)
+
+
+def test_unfit_nodes_are_left_out(oracle_mod):
+    """A node with NaN constants (Algorithm 3 could not fit it) does not change
+    the schedule: library and oracle give the sequence of the other nodes."""
+    from paper_1512_02818_gb300 import build, pdd
+    build.build()
+    rng = np.random.default_rng(14)
+    n = 12
+    K = rng.uniform(0.5, 3, n)
+    beta = rng.uniform(-1, -0.1, n)
+    alpha = rng.uniform(-2, 2, n)
+    V = rng.uniform(1, 6, n)
+    Vpsi = rng.uniform(20, 80, n)
+    rho = rng.uniform(-0.4, 0.4, n)
+    args = (1.0, 1.4, 0.01)
+    a_ref, s_ref = pdd.pdd_schedule(K, beta, alpha, V, Vpsi, rho, *args)
+    o_ref, os_ref = oracle_mod.schedule(K, beta, alpha, V, Vpsi, rho, *args)
+    nan = np.array([np.nan])
+    ext = [np.concatenate([v, nan]) for v in (K, beta, alpha, V, Vpsi, rho)]
+    a_nan, s_nan = pdd.pdd_schedule(*ext, *args)
+    o_nan, os_nan = oracle_mod.schedule(*ext, *args)
+    assert np.array_equal(a_nan, a_ref) and np.array_equal(s_nan, s_ref)
+    assert np.allclose(o_nan, o_ref, rtol=1e-12) and np.allclose(os_nan, os_ref, rtol=1e-12)
+    allnan = [np.full(3, np.nan) for _ in range(6)]
+    with pytest.raises(pdd.PddError):
+        pdd.pdd_schedule(*allnan, *args)
