@@ -47,16 +47,16 @@ TARGET_RMSE = 1e-3
 # Box-Muller, coefficients, updates, exit test, and for the control variate
 # the cell record, bilinear gradient and xi update), as executed: ncu's
 # smsp__thread_inst_executed.sum over the path-steps of the full-size launches
-# (profiles/paths_2d_c1_256nodes_1e5paths_counters.md; the planning estimates
-# were 110 and 150).
+# of this benchmark (a one-pass capture; the planning estimates were 110 and
+# 150).
 ALGO_INSTR = {"plain": 111.2, "cv": 140.1}
 # DRAM bytes (read + write) per launch of the dominant kernel (the eps = 1e-2
 # pass) from the same full-size capture; None whenever the kernel has changed
 # since that capture.
 NCU_TRAFFIC_BYTES = 1461248
 # Thread-instructions per path-step of the 3D control-variate kernel over the
-# full-size cascade launch (ncu smsp__thread_inst_executed.sum over its path-
-# steps, profiles/paths_3d_c2_cascade.md; the planning estimate was 190).
+# full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
+# over its path-steps, a one-pass capture; the planning estimate was 190).
 INSTR_3D = 228.3
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
@@ -591,6 +591,13 @@ def run_c2(args):
     prepared = [prob._prepare(l["nodes"], l["n_paths"], l["dt"], l["grid_id"], SEED,
                               l["stream_tag"], 1.0, False, True, False, False) for l in lv]
     largs, louts = [p[0] for p in prepared], [p[1] for p in prepared]
+    # launch shape from the autotuner on an eighth of the finest level (the
+    # level that holds 99 % of the cascade's path-steps)
+    tuned = (0, 0, None)
+    if not args.no_autotune:
+        sub = [torch.from_numpy(np.ascontiguousarray(nodes[::8, j])).to(dev) for j in range(3)]
+        tuned = prob.autotune(sub, levels_cfg[2]["n_paths"] // (10 * div), levels_cfg[2]["dt"],
+                              grid_id=2, stream_tag=77)
 
     def step():
         pdd.pdd_estimate_levels(prob.handle, largs, louts, pdd.PDD_FLAG_GRAPH | pdd.PDD_FLAG_ASYNC)
@@ -629,6 +636,9 @@ def run_c2(args):
                                    "persistent launch replayed from a CUDA graph",
                        "l2": "flushed between steps (256 MB)"},
             "nodes_per_s": len(nodes) * args.steps / (total_ms / 1e3),
+            "launch_shape": {"block_threads": tuned[0] or 128, "max_blocks": tuned[1],
+                             "chosen_by": "pdd_autotune on 1/8 of the finest level" if tuned[2]
+                             else "library default"},
             "levels": per_level, "graph_captures": ctx.graph_count(),
             "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
             "roofline": {"bound": "alu", "unit": "T thread-instr/s",

@@ -315,9 +315,12 @@ __device__ __forceinline__ bool cell_in_table(unsigned* err, int ix, int iy, int
 #endif
 }
 
+// Cell index min(max(floor(t), 0), n - 2) and the offset of t in it.  For
+// t >= 0 truncation is the floor, and for t < 0 both give an index that the
+// clamp takes to 0, so the truncating conversion gives the same cell and frac.
 template <class T>
 __device__ __forceinline__ int cell_of(T t, int n, T& frac) {
-  int i = (int)floor(t);
+  int i = (int)t;
   i = min(max(i, 0), n - 2);
   frac = t - (T)i;
   return i;
