@@ -47,13 +47,13 @@ TARGET_RMSE = 1e-3
 # Box-Muller, coefficients, updates, exit test, and for the control variate
 # the cell record, bilinear gradient and xi update), as executed: ncu's
 # smsp__thread_inst_executed.sum over the path-steps of the full-size launches
-# of this benchmark (a one-pass capture; the planning estimates were 110 and
-# 150).
-ALGO_INSTR = {"plain": 111.2, "cv": 140.1}
+# of this benchmark (a one-pass capture of the 4-steps-per-iteration kernels;
+# the planning estimates were 110 and 150).
+ALGO_INSTR = {"plain": 104.5, "cv": 134.2}
 # DRAM bytes (read + write) per launch of the dominant kernel (the eps = 1e-2
 # pass) from the same full-size capture; None whenever the kernel has changed
 # since that capture.
-NCU_TRAFFIC_BYTES = 1461248
+NCU_TRAFFIC_BYTES = 1509888
 # Thread-instructions per path-step of the 3D control-variate kernel over the
 # full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
 # over its path-steps, a one-pass capture; the planning estimate was 190).
@@ -463,6 +463,10 @@ def run_ours(args, rank, world, local):
         pred = r["var_phi"] / (kappa[name] * r["var_cv"])
         fixed[name]["predicted_speedup_median"] = float(np.median(pred))
         fixed[name]["kappa"] = kappa[name]
+        # the paper's cost unit (eq. F:VR_Pointwise_cost): path-steps, the
+        # controlled ones weighted by kappa -- the speedup the prediction is about
+        fixed[name]["work_speedup_vs_plain"] = (
+            fixed["plain"]["path_steps"] / (kappa[name] * fixed[name]["path_steps"]))
 
     # end to end through the C ABI with host buffers (pinned), copies included
     torch.cuda.synchronize()

@@ -43,6 +43,12 @@ constexpr int kMaxBlockThreads = 512;  // largest block size a launch may ask fo
 #define PDD_MIN_BLOCKS_3D 2  // 64 registers: twice the warps of the unconstrained 3D kernel
 #endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
+// Euler steps per iteration of the 2D kernel (between lane refills and exit
+// parking): 4 (two Philox blocks) halves the per-step share of the refill,
+// ring and loop work, but a lane whose path ends early in an iteration idles
+// for the rest of it, which costs on short paths; launches whose time steps
+// are all at most kLongPathH (paths of ~100 steps and more) take 4, others 2.
+constexpr double kLongPathH = 2e-3;
 enum { kCvNone = 0, kCvGrid = 1, kCvExact = 2 };
 
 // Per-lane path state.
@@ -486,7 +492,7 @@ __device__ __forceinline__ void init_lane(const PathArgs& a, PathState<T>& s, La
 // 65 registers a 512-thread block rounds up to 72 per thread and only one
 // block fits an SM, so it is capped at 64 (two blocks), which measured faster
 // than the uncapped build.
-template <class P, class T, int CV, bool MULTI>
+template <class P, class T, int CV, bool MULTI, int STEPS>
 __global__ void __launch_bounds__(kMaxBlockThreads, (MULTI && sizeof(T) == 4) ? 2
                                                                                : PDD_MIN_BLOCKS_2D)
     paths_2d(const __grid_constant__ PathArgs a) {
@@ -500,23 +506,28 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (MULTI && sizeof(T) == 4) ? 
   unsigned long long bnext = 0, bend = 0;
   while (refill<T, 2, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
     bool fin = false, trunc = false;
-    uint4 w = make_uint4(0, 0, 0, 0);
-    if (active) fin = should_finish<P, T, 2>(s, ls.thr0);
-    if (active && !fin) {
-      w = path_block<MULTI>(a, s.seg, (uint32_t)(s.k >> 1), s.path, s.node);
-      T n[3];
-      box_muller(w.x, w.y, n[0], n[1], ls.sqh);
-      n[2] = T(0);
-      euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
-      if (s.k >= ls.max_steps) fin = trunc = true;
-    }
-    if (active && !fin) fin = should_finish<P, T, 2>(s, ls.thr0);
-    if (active && !fin) {
-      T n[3];
-      box_muller(w.z, w.w, n[0], n[1], ls.sqh);
-      n[2] = T(0);
-      euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
-      if (s.k >= ls.max_steps) fin = trunc = true;
+    // STEPS / 2 Philox blocks per iteration, two steps each; the exit test
+    // precedes every step
+#pragma unroll
+    for (int half = 0; half < STEPS / 2; ++half) {
+      uint4 w = make_uint4(0, 0, 0, 0);
+      if (active && !fin) fin = should_finish<P, T, 2>(s, ls.thr0);
+      if (active && !fin) {
+        w = path_block<MULTI>(a, s.seg, (uint32_t)(s.k >> 1), s.path, s.node);
+        T n[3];
+        box_muller(w.x, w.y, n[0], n[1], ls.sqh);
+        n[2] = T(0);
+        euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) fin = trunc = true;
+      }
+      if (active && !fin) fin = should_finish<P, T, 2>(s, ls.thr0);
+      if (active && !fin) {
+        T n[3];
+        box_muller(w.z, w.w, n[0], n[1], ls.sqh);
+        n[2] = T(0);
+        euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) fin = trunc = true;
+      }
     }
     ring_exit<P, T, 2, MULTI>(a, ring, rc, s, active && fin, trunc);
     if (fin) active = false;
@@ -939,17 +950,31 @@ static cudaError_t launch_persistent(K kern, const PathArgs& a, int num_sms, cud
   return cudaGetLastError();
 }
 
+// Whether every segment of the launch has a time step of at most kLongPathH.
+static bool long_paths(const PathArgs& a) {
+  for (int i = 0; i < a.n_segs; ++i)
+    if (!(a.seg[i].h <= kLongPathH)) return false;
+  return true;
+}
+
 template <class P, class T, int CV, bool MULTI>
 static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, int* blocks) {
-  void (*kern)(PathArgs);
-  if constexpr (P::kDim == 3)
-    kern = paths_3d<P, T, CV, MULTI>;
-  else
-    kern = paths_2d<P, T, CV, MULTI>;
-  static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
-  static std::atomic<int> attr{0};
-  return launch_persistent(kern, a, num_sms, st, blocks, ExitRing<T, P::kDim>::kBytes, &attr,
-                           per_sm);
+  if constexpr (P::kDim == 3) {
+    static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
+    static std::atomic<int> attr{0};
+    return launch_persistent(paths_3d<P, T, CV, MULTI>, a, num_sms, st, blocks,
+                             ExitRing<T, 3>::kBytes, &attr, per_sm);
+  } else if (sizeof(T) == 4 && long_paths(a)) {  // FP64 paths: the step dominates
+    static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
+    static std::atomic<int> attr{0};
+    return launch_persistent(paths_2d<P, T, CV, MULTI, sizeof(T) == 4 ? 4 : 2>, a, num_sms, st,
+                             blocks, ExitRing<T, 2>::kBytes, &attr, per_sm);
+  } else {
+    static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
+    static std::atomic<int> attr{0};
+    return launch_persistent(paths_2d<P, T, CV, MULTI, 2>, a, num_sms, st, blocks,
+                             ExitRing<T, 2>::kBytes, &attr, per_sm);
+  }
 }
 
 template <class P, class T, int CV, bool MULTI>
@@ -958,7 +983,7 @@ static cudaError_t occupancy_one(int threads, int* occ) {
   if constexpr (P::kDim == 3)
     kern = paths_3d<P, T, CV, MULTI>;
   else
-    kern = paths_2d<P, T, CV, MULTI>;
+    kern = paths_2d<P, T, CV, MULTI, sizeof(T) == 4 ? 4 : 2>;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       occ, kern, threads, (size_t)(threads / 32) * ExitRing<T, P::kDim>::kBytes);
 }
