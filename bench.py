@@ -57,7 +57,7 @@ NCU_TRAFFIC_BYTES = 1509888
 # Thread-instructions per path-step of the 3D control-variate kernel over the
 # full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
 # over its path-steps, a one-pass capture; the planning estimate was 190).
-INSTR_3D = 228.3
+INSTR_3D = 223.6
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")

@@ -43,12 +43,16 @@ constexpr int kMaxBlockThreads = 512;  // largest block size a launch may ask fo
 #define PDD_MIN_BLOCKS_3D 2  // 64 registers: twice the warps of the unconstrained 3D kernel
 #endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
-// Euler steps per iteration of the 2D kernel (between lane refills and exit
-// parking): 4 (two Philox blocks) halves the per-step share of the refill,
-// ring and loop work, but a lane whose path ends early in an iteration idles
-// for the rest of it, which costs on short paths; launches whose time steps
-// are all at most kLongPathH (paths of ~100 steps and more) take 4, others 2.
+// Euler steps per iteration of the path kernels (between lane refills and
+// exit parking): 4 in 2D (two Philox blocks) and 8 in 3D (six) halve the
+// per-step share of the refill, ring and loop work against 2 and 4, but a
+// lane whose path ends early in an iteration idles for the rest of it, which
+// costs on short paths.  A launch takes the longer iterations when segments
+// with time steps above kLongPathH (paths of under ~100 steps) hold at most
+// kShortWorkShare of its expected path-steps (n_nodes x n_paths / h per
+// segment).
 constexpr double kLongPathH = 2e-3;
+constexpr double kShortWorkShare = 0.05;
 enum { kCvNone = 0, kCvGrid = 1, kCvExact = 2 };
 
 // Per-lane path state.
@@ -539,8 +543,9 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (MULTI && sizeof(T) == 4) ? 
 // 3D: steps 4j .. 4j+3 use normals 12j .. 12j+11, i.e. Philox blocks 3j,
 // 3j+1, 3j+2 (words a0..a3, b0..b3, c0..c3):
 //   step 0: a0 a1 a2   step 1: a3 b0 b1   step 2: b2 b3 c0   step 3: c1 c2 c3
-// Blocks are drawn only when the path is still running.
-template <class P, class T, int CV, bool MULTI>
+// Blocks are drawn only when the path is still running.  STEPS / 4 such
+// groups of four steps run per iteration (between lane refills).
+template <class P, class T, int CV, bool MULTI, int STEPS>
 __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
     paths_3d(const __grid_constant__ PathArgs a) {
   PathState<T> s;
@@ -553,48 +558,51 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
   unsigned long long bnext = 0, bend = 0;
   while (refill<T, 3, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
     bool fin = false, trunc = false;
-    T carry0 = T(0), carry1 = T(0);  // normals left over from the previous block
-    uint4 w = make_uint4(0, 0, 0, 0);
-    const uint32_t blk0 = 3u * ((uint32_t)s.k >> 2);
-    // step 0
-    if (active) fin = should_finish<P, T, 3>(s, ls.thr0);
-    if (active && !fin) {
-      w = path_block<MULTI>(a, s.seg, blk0, s.path, s.node);
-      T n[3], n3;
-      box_muller(w.x, w.y, n[0], n[1], ls.sqh);
-      box_muller(w.z, w.w, n[2], n3, ls.sqh);
-      carry0 = n3;
-      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
-      if (s.k >= ls.max_steps) fin = trunc = true;
-    }
-    // step 1
-    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
-    if (active && !fin) {
-      w = path_block<MULTI>(a, s.seg, blk0 + 1u, s.path, s.node);
-      T n[3];
-      n[0] = carry0;
-      box_muller(w.x, w.y, n[1], n[2], ls.sqh);
-      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
-      if (s.k >= ls.max_steps) fin = trunc = true;
-    }
-    // step 2
-    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
-    if (active && !fin) {
-      T n[3];
-      box_muller(w.z, w.w, n[0], n[1], ls.sqh);
-      w = path_block<MULTI>(a, s.seg, blk0 + 2u, s.path, s.node);
-      box_muller(w.x, w.y, n[2], carry1, ls.sqh);
-      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
-      if (s.k >= ls.max_steps) fin = trunc = true;
-    }
-    // step 3
-    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
-    if (active && !fin) {
-      T n[3];
-      n[0] = carry1;
-      box_muller(w.z, w.w, n[1], n[2], ls.sqh);
-      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
-      if (s.k >= ls.max_steps) fin = trunc = true;
+#pragma unroll
+    for (int quad = 0; quad < STEPS / 4; ++quad) {
+      T carry0 = T(0), carry1 = T(0);  // normals left over from the previous block
+      uint4 w = make_uint4(0, 0, 0, 0);
+      const uint32_t blk0 = 3u * ((uint32_t)s.k >> 2);
+      // step 0
+      if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+      if (active && !fin) {
+        w = path_block<MULTI>(a, s.seg, blk0, s.path, s.node);
+        T n[3], n3;
+        box_muller(w.x, w.y, n[0], n[1], ls.sqh);
+        box_muller(w.z, w.w, n[2], n3, ls.sqh);
+        carry0 = n3;
+        euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) fin = trunc = true;
+      }
+      // step 1
+      if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+      if (active && !fin) {
+        w = path_block<MULTI>(a, s.seg, blk0 + 1u, s.path, s.node);
+        T n[3];
+        n[0] = carry0;
+        box_muller(w.x, w.y, n[1], n[2], ls.sqh);
+        euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) fin = trunc = true;
+      }
+      // step 2
+      if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+      if (active && !fin) {
+        T n[3];
+        box_muller(w.z, w.w, n[0], n[1], ls.sqh);
+        w = path_block<MULTI>(a, s.seg, blk0 + 2u, s.path, s.node);
+        box_muller(w.x, w.y, n[2], carry1, ls.sqh);
+        euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) fin = trunc = true;
+      }
+      // step 3
+      if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+      if (active && !fin) {
+        T n[3];
+        n[0] = carry1;
+        box_muller(w.z, w.w, n[1], n[2], ls.sqh);
+        euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) fin = trunc = true;
+      }
     }
     ring_exit<P, T, 3, MULTI>(a, ring, rc, s, active && fin, trunc);
     if (fin) active = false;
@@ -950,21 +958,31 @@ static cudaError_t launch_persistent(K kern, const PathArgs& a, int num_sms, cud
   return cudaGetLastError();
 }
 
-// Whether every segment of the launch has a time step of at most kLongPathH.
-static bool long_paths(const PathArgs& a) {
-  for (int i = 0; i < a.n_segs; ++i)
-    if (!(a.seg[i].h <= kLongPathH)) return false;
-  return true;
+static bool long_iterations(const PathArgs& a) {
+  double all = 0.0, shorter = 0.0;
+  for (int i = 0; i < a.n_segs; ++i) {
+    const double w = (double)a.seg[i].total / a.seg[i].h;
+    all += w;
+    if (!(a.seg[i].h <= kLongPathH)) shorter += w;
+  }
+  return shorter <= kShortWorkShare * all;
 }
 
 template <class P, class T, int CV, bool MULTI>
 static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, int* blocks) {
+  const bool longer = sizeof(T) == 4 && long_iterations(a);  // FP64: the step dominates
   if constexpr (P::kDim == 3) {
+    if (longer) {
+      static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
+      static std::atomic<int> attr{0};
+      return launch_persistent(paths_3d<P, T, CV, MULTI, sizeof(T) == 4 ? 8 : 4>, a, num_sms,
+                               st, blocks, ExitRing<T, 3>::kBytes, &attr, per_sm);
+    }
     static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
     static std::atomic<int> attr{0};
-    return launch_persistent(paths_3d<P, T, CV, MULTI>, a, num_sms, st, blocks,
+    return launch_persistent(paths_3d<P, T, CV, MULTI, 4>, a, num_sms, st, blocks,
                              ExitRing<T, 3>::kBytes, &attr, per_sm);
-  } else if (sizeof(T) == 4 && long_paths(a)) {  // FP64 paths: the step dominates
+  } else if (longer) {
     static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
     static std::atomic<int> attr{0};
     return launch_persistent(paths_2d<P, T, CV, MULTI, sizeof(T) == 4 ? 4 : 2>, a, num_sms, st,
@@ -981,7 +999,7 @@ template <class P, class T, int CV, bool MULTI>
 static cudaError_t occupancy_one(int threads, int* occ) {
   void (*kern)(PathArgs);
   if constexpr (P::kDim == 3)
-    kern = paths_3d<P, T, CV, MULTI>;
+    kern = paths_3d<P, T, CV, MULTI, sizeof(T) == 4 ? 8 : 4>;
   else
     kern = paths_2d<P, T, CV, MULTI, sizeof(T) == 4 ? 4 : 2>;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
