@@ -388,10 +388,12 @@ def run_ours(args, rank, world, local):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.set_stream(ctx.stream)  # events, flushes and kernels on one stream
-    # launch shape from the library's autotuner, on one full control-variate pass
+    # launch shape and iteration from the library's autotuner, on one full
+    # control-variate pass
     tuned = (0, 0, None)
     if not args.no_autotune:
         tuned = prob.autotune(cols_dev, n_paths, DT, grid_id=1)
+    launch_iter = ctx.get_launch()[2]
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -505,6 +507,7 @@ def run_ours(args, rank, world, local):
         "timed_kernel_launches": n_timed,
         "launch_shape": {"block_threads": tuned[0] or (512 if n_nodes <= 512 else 128),
                          "max_blocks": tuned[1],
+                         "iteration": ["auto", "short", "long"][launch_iter],
                          "chosen_by": "pdd_autotune on the eps=1e-2 pass" if tuned[2]
                          else "library default"},
     }

@@ -210,6 +210,36 @@ int pdd_ctx_graph_count(pdd_ctx* ctx, int64_t* captures);
    The shape changes only the speed: the results are exact sums keyed by
    (node, path), identical for every shape.                                  */
 int pdd_ctx_set_launch(pdd_ctx* ctx, int block_threads, int max_blocks);
+/* Euler steps a path kernel takes per iteration, between lane refills (the
+   scheduling quantum): PDD_ITER_SHORT = 2 in 2D / 4 in 3D, PDD_ITER_LONG =
+   4 / 8 (FP32 paths; FP64 paths always take the short one), PDD_ITER_AUTO
+   (the default) = long when the segments with time steps above 2e-3 hold at
+   most 5 % of the launch's expected path-steps (n_nodes x n_paths / h), short
+   otherwise.  Longer iterations pay the refill and exit bookkeeping once per
+   more steps; a lane whose path ends early in an iteration idles for the rest
+   of it.  Like the launch shape, the choice changes only the speed (results
+   are exact sums keyed by node and path).  pdd_autotune sets it too.
+   pdd_ctx_get_launch reads the context's shape and iteration choice (any
+   output may be NULL).                                                     */
+#define PDD_ITER_AUTO 0
+#define PDD_ITER_SHORT 1
+#define PDD_ITER_LONG 2
+int pdd_ctx_set_iteration(pdd_ctx* ctx, int mode);
+int pdd_ctx_get_launch(pdd_ctx* ctx, int* block_threads, int* max_blocks, int* iteration);
+/* Stops the work in flight on the context (no counterpart in the paper):
+   callable from any thread, also while another thread waits inside an
+   estimate on this context.  The kernels take no further paths (a copy on a
+   stream of the context's own moves the launch's path cursor past its last
+   path; nothing on the device waits for it), the paths already running end
+   normally, and the call in flight returns PDD_ERR_CANCELLED with the
+   statistics of the paths that ran (n_paths per node tells how many).
+   Calls that start after pdd_ctx_abort returns are not affected.  If the call
+   in flight was about to finish it may report PDD_ERR_CANCELLED with every
+   path run.  Applies to pdd_estimate_nodes / _levels, pdd_accumulate, the
+   coupled calls and what runs on them (fit, MLMC); not to the
+   allocation-free call or to servers (use pdd_cancel).  It allocates
+   nothing: the context made its stream, event and 16 page-locked bytes.    */
+int pdd_ctx_abort(pdd_ctx* ctx);
 
 int pdd_create_problem(pdd_ctx* ctx, const pdd_problem_desc* desc, pdd_problem** out);
 int pdd_destroy_problem(pdd_problem* problem);
@@ -439,10 +469,13 @@ int pdd_schedule_predict(const pdd_schedule_args* s, double a, double aj, double
                          double* cost);
 
 /* Autotuner: runs `sample` (device coordinates) under candidate launch shapes
-   (128/256/512 threads per block, full and half occupancy), times each with
-   CUDA events on the context's stream, and keeps the fastest as the context's
-   launch shape (pdd_ctx_set_launch).  Outputs (nullable): the chosen shape and
-   its time.  Results of later calls do not depend on the choice.            */
+   (128/256/512 threads per block, full and half occupancy) with the automatic
+   iteration choice, then the fastest shape with the short and the long
+   iteration (pdd_ctx_set_iteration; FP32 paths), times each with CUDA events
+   on the context's stream, and keeps the fastest as the context's launch
+   shape and iteration.  Outputs (nullable): the chosen shape and its time
+   (pdd_ctx_get_launch gives the iteration).  Results of later calls do not
+   depend on the choice.                                                     */
 int pdd_autotune(pdd_problem* problem, const pdd_estimate_args* sample, int* best_threads,
                  int* best_max_blocks, double* best_ms);
 

@@ -4,7 +4,9 @@
 // Algorithm 1 and Sec. 2.2-3.1).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +49,12 @@ int error_word_status(unsigned err, const char* who) {
   return PDD_OK;
 }
 
+static int aborted_status(const char* who) {
+  set_error("%s: aborted by pdd_ctx_abort; the results hold the paths that ran (n_paths per "
+            "node)", who);
+  return PDD_ERR_CANCELLED;
+}
+
 static int cuda_fail(cudaError_t e, const char* what) {
   set_error("%s: CUDA error %d (%s)", what, (int)e, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? PDD_ERR_NOMEM : PDD_ERR_CUDA;
@@ -78,9 +86,17 @@ struct pdd_ctx {
   int64_t launches = 0;
   int block_threads = 0;  // launch shape (0: defaults), set by pdd_ctx_set_launch / pdd_autotune
   int max_blocks = 0;
+  int iter_mode = PDD_ITER_AUTO;  // steps per iteration (pdd_ctx_set_iteration / pdd_autotune)
   cudaGraphExec_t gexec = nullptr;  // cached graph of the last PDD_FLAG_GRAPH call
   uint64_t gkey = 0;
   int64_t graph_captures = 0;
+  // pdd_ctx_abort: copies into the workspace header on a stream of its own
+  // (created at the first abort), ordered before the next call's header reset
+  std::mutex abort_mu;  // held while the workspace is replaced and while an abort is enqueued
+  cudaStream_t abort_stream = nullptr;
+  cudaEvent_t abort_ev = nullptr;
+  unsigned long long* abort_src = nullptr;  // page-locked: {cursor past any launch, flag}
+  std::atomic<bool> abort_pending{false};
 };
 
 struct GridSlot {
@@ -95,13 +111,21 @@ struct pdd_problem {
   GridSlot grids[PDD_MAX_GRIDS];
 };
 
-// Workspace header (first 256 bytes).
+// Workspace header (first 256 bytes).  pdd_ctx_abort writes a cursor past
+// any launch's paths (so no warp takes another batch) and sets `aborted`.
 struct WsHeader {
   unsigned long long cursor;
   unsigned err;
-  unsigned pad;
+  unsigned aborted;
   unsigned long long trunc_total;
 };
+static_assert(offsetof(WsHeader, aborted) == 12, "abort flag offset");
+
+// Orders the context stream after an abort enqueued since its last call, so
+// that the abort's copies land before this call resets the header.
+static void wait_abort(pdd_ctx* c) {
+  if (c->abort_pending.exchange(false)) cudaStreamWaitEvent(c->stream, c->abort_ev, 0);
+}
 
 namespace pdd {
 // Device, SM count and launch shape of a context, for the serving runtime.
@@ -114,6 +138,7 @@ bool ctx_view(pdd_ctx* c, int* device, int* num_sms, int* block_threads, int* ma
   return true;
 }
 pdd_ctx* problem_ctx(pdd_problem* p) { return p ? p->ctx : nullptr; }
+int ctx_iter_mode(pdd_ctx* c) { return c ? c->iter_mode : PDD_ITER_AUTO; }
 }  // namespace pdd
 
 namespace pdd {
@@ -147,6 +172,9 @@ static int ensure_workspace(pdd_ctx* c, size_t bytes) {
     return PDD_ERR_NOMEM;
   }
   PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  // no abort copy may still target the buffer about to be freed
+  std::lock_guard<std::mutex> ak(c->abort_mu);
+  if (c->abort_stream) PDD_CUDA(cudaStreamSynchronize(c->abort_stream), "cudaStreamSynchronize");
   if (c->ws) {
     cudaFree(c->ws);
     c->ws = nullptr;
@@ -324,6 +352,7 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
   pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
   pa.max_blocks = c->max_blocks;
   pa.block_threads = c->block_threads;
+  pa.iter_mode = c->iter_mode;
   const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
   uint32_t rec_base[PDD_MAX_LEVELS];
   {
@@ -462,10 +491,12 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
       c->gkey = key;
       c->graph_captures += 1;
     }
+    wait_abort(c);
     if (c->timing) PDD_CUDA(cudaEventRecord(ev0, c->stream), "cudaEventRecord");
     PDD_CUDA(cudaGraphLaunch(c->gexec, c->stream), "cudaGraphLaunch");
     if (c->timing) PDD_CUDA(cudaEventRecord(ev1, c->stream), "cudaEventRecord");
   } else {
+    wait_abort(c);
     PDD_CUDA(cudaMemsetAsync(ws, 0, off_acc + total_nodes * kAccWords * 8, c->stream),
              "cudaMemsetAsync");
     if (c->timing) PDD_CUDA(cudaEventRecord(ev0, c->stream), "cudaEventRecord");
@@ -505,6 +536,7 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
   PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync(header)");
   PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (h.aborted) return aborted_status(who);
   if (h.err != 0u) return error_word_status(h.err, who);
   if (h.cursor < pa.total) {
     set_error("%s: internal error, %llu of %llu paths scheduled", who, h.cursor, pa.total);
@@ -548,6 +580,20 @@ int pdd_ctx_create(int device, void* cuda_stream, size_t mem_budget, pdd_ctx** o
   c->device = device;
   c->budget = mem_budget;
   c->num_sms = sms;
+  // what pdd_ctx_abort uses, made now so that an abort allocates nothing (page-locked
+  // allocation can wait for the device)
+  cudaError_t ea = cudaStreamCreateWithFlags(&c->abort_stream, cudaStreamNonBlocking);
+  if (ea == cudaSuccess) ea = cudaEventCreateWithFlags(&c->abort_ev, cudaEventDisableTiming);
+  if (ea == cudaSuccess)
+    ea = cudaMallocHost((void**)&c->abort_src, 2 * sizeof(unsigned long long));
+  if (ea != cudaSuccess) {
+    if (c->abort_ev) cudaEventDestroy(c->abort_ev);
+    if (c->abort_stream) cudaStreamDestroy(c->abort_stream);
+    delete c;
+    return cuda_fail(ea, "pdd_ctx_create: abort resources");
+  }
+  c->abort_src[0] = 1ull << 62;  // past the index space of any launch (< 2^62 paths)
+  c->abort_src[1] = 1ull;        // low word: the header's `aborted`
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -572,6 +618,12 @@ void pdd_ctx_destroy(pdd_ctx* c) {
       cudaEventDestroy(ev.second);
     }
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->abort_stream) {
+      cudaStreamSynchronize(c->abort_stream);
+      cudaStreamDestroy(c->abort_stream);
+      cudaEventDestroy(c->abort_ev);
+      cudaFreeHost(c->abort_src);
+    }
     if (c->ws) cudaFree(c->ws);
     if (c->own_stream) cudaStreamDestroy(c->stream);
   }
@@ -652,6 +704,24 @@ int pdd_ctx_launch_count(pdd_ctx* c, int64_t* launches) {
     return PDD_ERR_INVALID;
   }
   *launches = c->launches;
+  return PDD_OK;
+}
+
+int pdd_ctx_abort(pdd_ctx* c) {
+  if (!c) {
+    set_error("pdd_ctx_abort: NULL context");
+    return PDD_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->abort_mu);
+  DeviceGuard g(c->device);
+  if (!c->ws) return PDD_OK;  // nothing has run on this context yet
+  PDD_CUDA(cudaMemcpyAsync((char*)c->ws + offsetof(WsHeader, aborted), &c->abort_src[1], 4,
+                           cudaMemcpyHostToDevice, c->abort_stream),
+           "cudaMemcpyAsync(abort flag)");
+  PDD_CUDA(cudaMemcpyAsync(c->ws, &c->abort_src[0], 8, cudaMemcpyHostToDevice, c->abort_stream),
+           "cudaMemcpyAsync(abort cursor)");
+  PDD_CUDA(cudaEventRecord(c->abort_ev, c->abort_stream), "cudaEventRecord");
+  c->abort_pending = true;
   return PDD_OK;
 }
 
@@ -863,6 +933,7 @@ int pdd_accumulate(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_off
   pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
   pa.max_blocks = c->max_blocks;
   pa.block_threads = c->block_threads;
+  pa.iter_mode = c->iter_mode;
   pa.n_segs = 1;
   SegArgs& sg = pa.seg[0];
   const int dim = p->dim;
@@ -887,6 +958,7 @@ int pdd_accumulate(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_off
   sg.grid_n = lp.grid_n;
   sg.max_steps = (int)lp.max_steps;
   pa.total = sg.total;
+  wait_abort(c);
   PDD_CUDA(cudaMemsetAsync(hdr, 0, 256, c->stream), "cudaMemsetAsync");
   int blocks = 0;
   PDD_CUDA(launch_paths(p->desc.kind, p->desc.precision, lp.cv, pa, c->num_sms, c->stream, &blocks),
@@ -897,6 +969,7 @@ int pdd_accumulate(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_off
   PDD_CUDA(cudaMemcpyAsync(&h, hdr, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync(header)");
   PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (h.aborted) return aborted_status("pdd_accumulate");
   if (h.err != 0u) return error_word_status(h.err, "pdd_accumulate");
   if (h.trunc_total > 0) {
     set_error("pdd_accumulate: %llu paths hit max_steps", h.trunc_total);
@@ -993,6 +1066,7 @@ static int coupled_launch(pdd_problem* p, const pdd_estimate_args* a, const Leve
   pa.y_exp = p->desc.y_rule == PDD_Y_EXP;
   pa.max_blocks = c->max_blocks;
   pa.block_threads = c->block_threads;
+  pa.iter_mode = c->iter_mode;
   pa.n_segs = 2;
   pa.total = (unsigned long long)n * (unsigned long long)a->n_paths;
   const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
@@ -1024,6 +1098,7 @@ static int coupled_launch(pdd_problem* p, const pdd_estimate_args* a, const Leve
     sg.grid_n = lp.grid_n;
     sg.max_steps = steps_cap(h);
   }
+  wait_abort(c);
   PDD_CUDA(cudaMemsetAsync(hdr, 0, 256, c->stream), "cudaMemsetAsync");
   int blocks = 0;
   char what[96];
@@ -1040,6 +1115,7 @@ static int coupled_status(pdd_ctx* c, const char* who) {
   PDD_CUDA(cudaMemcpyAsync(&h, c->ws, sizeof(h), cudaMemcpyDeviceToHost, c->stream),
            "cudaMemcpyAsync(header)");
   PDD_CUDA(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (h.aborted) return aborted_status(who);
   if (h.err != 0u) return error_word_status(h.err, who);
   if (h.trunc_total > 0) {
     set_error("%s: %llu paths hit max_steps", who, h.trunc_total);
@@ -1157,6 +1233,28 @@ int pdd_ctx_set_launch(pdd_ctx* c, int block_threads, int max_blocks) {
   return PDD_OK;
 }
 
+int pdd_ctx_set_iteration(pdd_ctx* c, int mode) {
+  if (!c || (mode != PDD_ITER_AUTO && mode != PDD_ITER_SHORT && mode != PDD_ITER_LONG)) {
+    set_error("pdd_ctx_set_iteration: NULL context or mode not PDD_ITER_AUTO/SHORT/LONG");
+    return PDD_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->iter_mode = mode;
+  return PDD_OK;
+}
+
+int pdd_ctx_get_launch(pdd_ctx* c, int* block_threads, int* max_blocks, int* iteration) {
+  if (!c) {
+    set_error("pdd_ctx_get_launch: NULL context");
+    return PDD_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (block_threads) *block_threads = c->block_threads;
+  if (max_blocks) *max_blocks = c->max_blocks;
+  if (iteration) *iteration = c->iter_mode;
+  return PDD_OK;
+}
+
 int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_threads,
                  int* best_max_blocks, double* best_ms) {
   if (!p || !sample) {
@@ -1185,10 +1283,38 @@ int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_thre
   out.mean_phi = dmean;
   pdd_estimate_args a = *sample;
   a.flags &= ~(PDD_FLAG_EMIT_PATHS | PDD_FLAG_ASYNC);
-  const int threads_c[3] = {128, 256, 512};
-  int bt = 0, bb = 0;
-  double bms = 1e300;
+  const int old_iter = c->iter_mode;
   int rc = PDD_OK;
+  // CUDA-event time of the sample under the context's current settings (the
+  // first of two runs warms up)
+  auto time_one = [&]() -> double {
+    double ms = 0.0;
+    for (int rep = 0; rep < 2 && rc >= 0; ++rep) {
+      cudaEvent_t e0, e1;
+      {
+        DeviceGuard g(c->device);
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, c->stream);
+      }
+      rc = pdd_estimate_nodes(p, &a, &out);
+      {
+        DeviceGuard g(c->device);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float f = 0.f;
+        cudaEventElapsedTime(&f, e0, e1);
+        ms = f;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+      }
+    }
+    return ms;
+  };
+  const int threads_c[3] = {128, 256, 512};
+  int bt = 0, bb = 0, bi = PDD_ITER_AUTO;
+  double bms = 1e300;
+  pdd_ctx_set_iteration(c, PDD_ITER_AUTO);
   for (int ti = 0; ti < 3 && rc >= 0; ++ti) {
     // full occupancy, and half of it (fewer resident warps, less L1 pressure)
     for (int frac = 0; frac < 2 && rc >= 0; ++frac) {
@@ -1200,33 +1326,23 @@ int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_thre
         max_blocks = (occ / 2 > 0 ? occ / 2 : 1) * c->num_sms;
       }
       pdd_ctx_set_launch(c, threads_c[ti], max_blocks);
-      double ms = 0.0;
-      for (int rep = 0; rep < 2 && rc >= 0; ++rep) {  // first run warms up
-        double t0 = 0.0;
-        cudaEvent_t e0, e1;
-        {
-          DeviceGuard g(c->device);
-          cudaEventCreate(&e0);
-          cudaEventCreate(&e1);
-          cudaEventRecord(e0, c->stream);
-        }
-        rc = pdd_estimate_nodes(p, &a, &out);
-        {
-          DeviceGuard g(c->device);
-          cudaEventRecord(e1, c->stream);
-          cudaEventSynchronize(e1);
-          float f = 0.f;
-          cudaEventElapsedTime(&f, e0, e1);
-          t0 = f;
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-        }
-        ms = t0;
-      }
+      const double ms = time_one();
       if (rc >= 0 && ms < bms) {
         bms = ms;
         bt = threads_c[ti];
         bb = max_blocks;
+      }
+    }
+  }
+  // the scheduling quantum (steps per iteration) at the fastest shape
+  if (rc >= 0 && p->desc.precision == PDD_PATH_FP32) {
+    pdd_ctx_set_launch(c, bt, bb);
+    for (int mode : {PDD_ITER_SHORT, PDD_ITER_LONG}) {
+      pdd_ctx_set_iteration(c, mode);
+      const double ms = time_one();
+      if (rc >= 0 && ms < bms) {
+        bms = ms;
+        bi = mode;
       }
     }
   }
@@ -1236,9 +1352,11 @@ int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_thre
   }
   if (rc < 0) {
     pdd_ctx_set_launch(c, old_threads, old_blocks);
+    pdd_ctx_set_iteration(c, old_iter);
     return rc;
   }
   pdd_ctx_set_launch(c, bt, bb);
+  pdd_ctx_set_iteration(c, bi);
   if (best_threads) *best_threads = bt;
   if (best_max_blocks) *best_max_blocks = bb;
   if (best_ms) *best_ms = bms;

@@ -71,6 +71,7 @@ struct PathArgs {
   int y_exp;
   int max_blocks;              // 0 = occupancy x SM count
   int block_threads;           // 0 = default (256)
+  int iter_mode;               // Euler steps per iteration: PDD_ITER_AUTO / _SHORT / _LONG
   int n_segs;                  // 1 .. kMaxSegments; segments in increasing `begin`
   uint32_t cache_nodes;        // record slots cached in shared memory per block (0: none);
                                // set by the launchers
@@ -133,6 +134,7 @@ static_assert(PDD_MAX_GRIDS == 8, "ProblemView holds 8 grid slots");
 int error_word_status(unsigned err, const char* who);
 bool problem_view(pdd_problem* p, ProblemView* v);
 bool ctx_view(pdd_ctx* c, int* device, int* num_sms, int* block_threads, int* max_blocks);
+int ctx_iter_mode(pdd_ctx* c);  // the context's PDD_ITER_* choice
 pdd_ctx* problem_ctx(pdd_problem* p);
 
 cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int num_sms,

@@ -970,7 +970,9 @@ static bool long_iterations(const PathArgs& a) {
 
 template <class P, class T, int CV, bool MULTI>
 static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, int* blocks) {
-  const bool longer = sizeof(T) == 4 && long_iterations(a);  // FP64: the step dominates
+  // FP64 paths: the step dominates, they always take the short iteration
+  const bool longer = sizeof(T) == 4 && (a.iter_mode == PDD_ITER_LONG ||
+                                         (a.iter_mode == PDD_ITER_AUTO && long_iterations(a)));
   if constexpr (P::kDim == 3) {
     if (longer) {
       static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];

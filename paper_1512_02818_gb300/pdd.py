@@ -104,6 +104,7 @@ class ServerDesc(ctypes.Structure):
 
 
 PDD_SERVE_FAIR, PDD_SERVE_SHORTEST, PDD_SERVE_EARLIEST_DEADLINE = 0, 1, 2
+PDD_ITER_AUTO, PDD_ITER_SHORT, PDD_ITER_LONG = 0, 1, 2
 
 
 class MlmcArgs(ctypes.Structure):
@@ -155,6 +156,11 @@ _SIGS = [
     ("pdd_ctx_launch_count", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     ("pdd_ctx_graph_count", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     ("pdd_ctx_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    ("pdd_ctx_abort", ctypes.c_int, [ctypes.c_void_p]),
+    ("pdd_ctx_set_iteration", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("pdd_ctx_get_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
     ("pdd_estimate_levels", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                            ctypes.POINTER(EstimateArgs),
                                            ctypes.POINTER(NodeStats), ctypes.c_uint32]),
@@ -549,6 +555,21 @@ class Context:
 
     def set_launch(self, block_threads: int = 0, max_blocks: int = 0) -> None:
         pdd_ctx_set_launch(self.handle, block_threads, max_blocks)
+
+    def set_iteration(self, mode: int) -> None:
+        """Euler steps per iteration: PDD_ITER_AUTO / _SHORT / _LONG."""
+        _check(self._lib.pdd_ctx_set_iteration(self.handle, mode))
+
+    def get_launch(self) -> tuple[int, int, int]:
+        """(block_threads, max_blocks, iteration mode) of the context."""
+        v = [ctypes.c_int() for _ in range(3)]
+        _check(self._lib.pdd_ctx_get_launch(self.handle, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def abort(self) -> None:
+        """Stop the work in flight on this context (pdd_ctx_abort); safe to
+        call from another thread while an estimate runs."""
+        _check(self._lib.pdd_ctx_abort(self.handle))
 
     def close(self) -> None:
         if self.handle:

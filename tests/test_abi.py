@@ -71,6 +71,7 @@ def test_error_paths_without_gpu(libpdd):
     assert b"NULL" in lib.pdd_last_error()
     assert lib.pdd_create_problem(None, None, None) == libpdd.PDD_ERR_INVALID
     assert lib.pdd_ctx_set_timing(None, 1) == libpdd.PDD_ERR_INVALID
+    assert lib.pdd_ctx_abort(None) == libpdd.PDD_ERR_INVALID
     assert lib.pdd_debug_philox(None, None, None, -1) == libpdd.PDD_ERR_INVALID
     lib.pdd_ctx_destroy(None)  # no-op
     assert lib.pdd_destroy_problem(None) == libpdd.PDD_OK

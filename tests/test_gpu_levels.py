@@ -125,12 +125,31 @@ def test_launch_shape_and_autotuner_do_not_change_results(env):
     for threads, max_blocks in ((128, 0), (512, 0), (256, 4), (64, 1), (0, 0)):
         ctx.set_launch(threads, max_blocks)
         _same(pdd, ref, prob.estimate(nodes, 900, 1e-3, grid_id=0))
+    # steps per iteration (scheduling quantum): short, long and automatic, on a
+    # 2D and a 3D problem
+    for mode in (pdd.PDD_ITER_SHORT, pdd.PDD_ITER_LONG, pdd.PDD_ITER_AUTO):
+        ctx.set_iteration(mode)
+        _same(pdd, ref, prob.estimate(nodes, 900, 1e-3, grid_id=0))
+    p3 = pdd.Problem(ctx, pdd.PDD_PROBLEM_CUBE_3D)
+    p3.set_control_grid(0, W.control_grid(2, 33, 1e-2))
+    n3 = W.workload_nodes("c2")[::97]
+    ref3 = p3.estimate(n3, 300, 1e-3, grid_id=0)
+    for mode in (pdd.PDD_ITER_SHORT, pdd.PDD_ITER_LONG):
+        ctx.set_iteration(mode)
+        _same(pdd, ref3, p3.estimate(n3, 300, 1e-3, grid_id=0))
+    ctx.set_iteration(pdd.PDD_ITER_AUTO)
+    p3.close()
     t, b, ms = prob.autotune(nodes, 900, 1e-3, grid_id=0)
     assert t in (128, 256, 512) and b >= 0 and ms > 0
+    assert ctx.get_launch()[:2] == (t, b)
+    assert ctx.get_launch()[2] in (pdd.PDD_ITER_AUTO, pdd.PDD_ITER_SHORT, pdd.PDD_ITER_LONG)
     _same(pdd, ref, prob.estimate(nodes, 900, 1e-3, grid_id=0))
     with pytest.raises(pdd.PddError):
         ctx.set_launch(100, 0)
+    with pytest.raises(pdd.PddError):
+        ctx.set_iteration(7)
     ctx.set_launch(0, 0)
+    ctx.set_iteration(pdd.PDD_ITER_AUTO)
     prob.close()
 
 
