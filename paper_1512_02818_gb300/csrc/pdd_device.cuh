@@ -46,6 +46,22 @@ __device__ __forceinline__ double m_exp(double x) { return exp(x); }
 __device__ __forceinline__ void m_sincos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 
+// Explicitly rounded arithmetic.  A multiply and an add written as separate
+// operators may or may not be fused into one FMA, and the compiler decides
+// per inlined copy of the code (the path step is inlined into the ordinary
+// and the drain iterations of every kernel variant).  The arithmetic whose
+// result must not depend on that choice -- the grid interpolation, the
+// control-variate increment and the compensated sums -- uses these, which
+// are never contracted, so a path computes the same bits in every copy.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
 // Uniform (0,1) from a 32-bit word: ((w >> 9) + 1/2) 2^-23, exact in FP32.
 __device__ __forceinline__ float unit_f(uint32_t w) {
   return fmaf((float)(w >> 9), 0x1p-23f, 0x1p-24f);
@@ -95,16 +111,16 @@ struct Coef {
 template <class T, bool GRAD>
 __device__ __forceinline__ void exp_cos_2d(T x, T y, Coef<T>& o, T& u) {
   const T sy = m_sin(y), cx = m_cos(x);
-  const T E = m_exp(x + y);
+  const T E = m_exp(add_rn(x, y));
   T sn, cs;
-  m_sincos(x - y, &sn, &cs);
-  u = E * cs;
-  const T ux = E * (cs - sn), uy = E * (cs + sn);
-  o.b0 = T(0.5) * sy;
-  o.b1 = T(0.5) * cx;
+  m_sincos(sub_rn(x, y), &sn, &cs);
+  u = mul_rn(E, cs);
+  const T ux = mul_rn(E, sub_rn(cs, sn)), uy = mul_rn(E, add_rn(cs, sn));
+  o.b0 = mul_rn(T(0.5), sy);
+  o.b1 = mul_rn(T(0.5), cx);
   o.b2 = T(0);
-  o.c = T(1) + x * x + y * y;
-  o.f = o.b0 * ux + o.b1 * uy - o.c * u;
+  o.c = fma_rn(y, y, fma_rn(x, x, T(1)));                   // 1 + x^2 + y^2
+  o.f = fma_rn(o.b1, uy, fma_rn(o.b0, ux, mul_rn(-o.c, u)));  // b . grad u - c u
   o.g0 = ux;
   o.g1 = uy;
   o.g2 = T(0);
@@ -123,7 +139,7 @@ struct Cfg0 {
   }
   template <class T>
   __device__ __forceinline__ static T g(T x, T y, T) {
-    return m_exp(x + y) * m_cos(x - y);
+    return mul_rn(m_exp(add_rn(x, y)), m_cos(sub_rn(x, y)));
   }
   template <class T>
   __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1); }
@@ -137,7 +153,8 @@ struct Aniso {
   // a(x) = 1 + sin(2 pi x)/2, with sin(2 pi x) = -sin(2 pi (x - 1/2)).
   template <class T>
   __device__ __forceinline__ static T a_of(T x) {
-    return T(1) - T(0.5) * m_sin(T(6.283185307179586476925286766559) * (x - T(0.5)));
+    return fma_rn(T(-0.5), m_sin(mul_rn(T(6.283185307179586476925286766559), sub_rn(x, T(0.5)))),
+                  T(1));
   }
   template <class T, bool GRAD>
   __device__ __forceinline__ static void eval(T x, T y, T, Coef<T>& o) {
@@ -145,12 +162,12 @@ struct Aniso {
     exp_cos_2d<T, GRAD>(x, y, o, u);
     const T a = a_of(x);
     // 1/2 sum a_ij u_ij = 1/2 * 2 * (a/2) * u_xy with u_xy = 2u
-    o.f += a * u;
+    o.f = fma_rn(a, u, o.f);
     o.sa = m_sqrt(a);
   }
   template <class T>
   __device__ __forceinline__ static T g(T x, T y, T) {
-    return m_exp(x + y) * m_cos(x - y);
+    return mul_rn(m_exp(add_rn(x, y)), m_cos(sub_rn(x, y)));
   }
   template <class T>
   __device__ __forceinline__ static T exit_scale(T x, T, T) { return m_sqrt(a_of(x)); }
@@ -173,19 +190,19 @@ struct Cube3 {
       cz = m_cos(z);
       cy = sz = T(0);
     }
-    const T e = ex * sy * cz;
+    const T e = mul_rn(mul_rn(ex, sy), cz);
     o.b0 = o.b1 = o.b2 = T(0);
     o.c = T(1);
     // 1/2 Delta u - u with Delta u = -e^x sin y cos z
-    o.f = T(-1.5) * e - x * y * z;
-    o.g0 = e + y * z;
-    o.g1 = ex * cy * cz + x * z;
-    o.g2 = -ex * sy * sz + x * y;
+    o.f = fma_rn(T(-1.5), e, -mul_rn(mul_rn(x, y), z));
+    o.g0 = fma_rn(y, z, e);
+    o.g1 = fma_rn(x, z, mul_rn(mul_rn(ex, cy), cz));
+    o.g2 = fma_rn(x, y, -mul_rn(mul_rn(ex, sy), sz));
     o.sa = T(1);
   }
   template <class T>
   __device__ __forceinline__ static T g(T x, T y, T z) {
-    return m_exp(x) * m_sin(y) * m_cos(z) + x * y * z;
+    return fma_rn(mul_rn(x, y), z, mul_rn(mul_rn(m_exp(x), m_sin(y)), m_cos(z)));
   }
   template <class T>
   __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1); }
@@ -201,20 +218,21 @@ struct PaperEx {
   template <class T, bool GRAD>
   __device__ __forceinline__ static void eval(T x, T y, T, Coef<T>& o) {
     T sp, cp, sq, cq, ss, cs;
-    const T p = T(2) * x * (y - T(2)), q = T(3) * y * (x - T(2));
+    const T ym2 = sub_rn(y, T(2)), xm2 = sub_rn(x, T(2));
+    const T p = mul_rn(mul_rn(T(2), x), ym2), q = mul_rn(mul_rn(T(3), y), xm2);
     m_sincos(p, &sp, &cp);
     m_sincos(q, &sq, &cq);
-    m_sincos(x + y, &ss, &cs);
-    const T inv = T(1) / (T(1.1) + ss);
-    const T u = T(2) * cp + sq + T(3.1);
-    const T ux = T(-4) * (y - T(2)) * sp + T(3) * y * cq;
-    const T uy = T(-4) * x * sp + T(3) * (x - T(2)) * cq;
-    const T ym2 = y - T(2), xm2 = x - T(2);
-    const T lap = T(-8) * (ym2 * ym2 + x * x) * cp - T(9) * (y * y + xm2 * xm2) * sq;
-    o.b0 = o.b1 = cs * inv;
+    m_sincos(add_rn(x, y), &ss, &cs);
+    const T inv = T(1) / add_rn(T(1.1), ss);
+    const T u = add_rn(fma_rn(T(2), cp, sq), T(3.1));
+    const T ux = fma_rn(mul_rn(T(3), y), cq, mul_rn(mul_rn(T(-4), ym2), sp));
+    const T uy = fma_rn(mul_rn(T(3), xm2), cq, mul_rn(mul_rn(T(-4), x), sp));
+    const T lap = fma_rn(mul_rn(T(-9), fma_rn(xm2, xm2, mul_rn(y, y))), sq,
+                         mul_rn(mul_rn(T(-8), fma_rn(x, x, mul_rn(ym2, ym2))), cp));
+    o.b0 = o.b1 = mul_rn(cs, inv);
     o.b2 = T(0);
-    o.c = (x * x + y * y) * inv;
-    o.f = lap + o.b0 * (ux + uy) - o.c * u;
+    o.c = mul_rn(fma_rn(y, y, mul_rn(x, x)), inv);
+    o.f = fma_rn(-o.c, u, fma_rn(o.b0, add_rn(ux, uy), lap));
     o.g0 = ux;
     o.g1 = uy;
     o.g2 = T(0);
@@ -222,7 +240,9 @@ struct PaperEx {
   }
   template <class T>
   __device__ __forceinline__ static T g(T x, T y, T) {
-    return T(2) * m_cos(T(2) * x * (y - T(2))) + m_sin(T(3) * y * (x - T(2))) + T(3.1);
+    return add_rn(fma_rn(T(2), m_cos(mul_rn(mul_rn(T(2), x), sub_rn(y, T(2)))),
+                         m_sin(mul_rn(mul_rn(T(3), y), sub_rn(x, T(2))))),
+                  T(3.1));
   }
   template <class T>
   __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1.41421356237309504880); }
@@ -244,7 +264,7 @@ struct Harmonic {
     o.sa = T(1);
   }
   template <class T>
-  __device__ __forceinline__ static T g(T x, T y, T) { return x * x - y * y; }
+  __device__ __forceinline__ static T g(T x, T y, T) { return fma_rn(x, x, -mul_rn(y, y)); }
   template <class T>
   __device__ __forceinline__ static T exit_scale(T, T, T) { return T(1); }
 };
@@ -315,14 +335,15 @@ __device__ __forceinline__ bool cell_in_table(unsigned* err, int ix, int iy, int
 #endif
 }
 
-// Cell index min(max(floor(t), 0), n - 2) and the offset of t in it.  For
-// t >= 0 truncation is the floor, and for t < 0 both give an index that the
-// clamp takes to 0, so the truncating conversion gives the same cell and frac.
+// Cell index min(max(floor(x s), 0), n - 2) and the offset of x s in it,
+// frac = x s - i with one rounding.  For x s >= 0 truncation is the floor,
+// and for x s < 0 both give an index that the clamp takes to 0, so the
+// truncating conversion gives the same cell and frac.
 template <class T>
-__device__ __forceinline__ int cell_of(T t, int n, T& frac) {
-  int i = (int)t;
+__device__ __forceinline__ int cell_of(T x, T s, int n, T& frac) {
+  int i = (int)mul_rn(x, s);
   i = min(max(i, 0), n - 2);
-  frac = t - (T)i;
+  frac = fma_rn(x, s, -(T)i);
   return i;
 }
 
@@ -331,17 +352,19 @@ __device__ __forceinline__ void grid_grad_2d(const float2* __restrict__ G, int n
                                              T& gy, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy;
-  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy);
+  const int ix = cell_of(x, s, n, fx), iy = cell_of(y, s, n, fy);
   if (!cell_in_table(err, ix, iy, 0, n)) {
     gx = gy = T(0);
     return;
   }
   const float2* p = G + (size_t)iy * n + ix;
   const float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + n), d = __ldg(p + n + 1);
-  const T lx0 = (T)a.x + fx * ((T)b.x - (T)a.x), lx1 = (T)c.x + fx * ((T)d.x - (T)c.x);
-  const T ly0 = (T)a.y + fx * ((T)b.y - (T)a.y), ly1 = (T)c.y + fx * ((T)d.y - (T)c.y);
-  gx = lx0 + fy * (lx1 - lx0);
-  gy = ly0 + fy * (ly1 - ly0);
+  const T lx0 = fma_rn(fx, sub_rn((T)b.x, (T)a.x), (T)a.x);
+  const T lx1 = fma_rn(fx, sub_rn((T)d.x, (T)c.x), (T)c.x);
+  const T ly0 = fma_rn(fx, sub_rn((T)b.y, (T)a.y), (T)a.y);
+  const T ly1 = fma_rn(fx, sub_rn((T)d.y, (T)c.y), (T)c.y);
+  gx = fma_rn(fy, sub_rn(lx1, lx0), lx0);
+  gy = fma_rn(fy, sub_rn(ly1, ly0), ly0);
 }
 
 template <class T>
@@ -349,7 +372,8 @@ __device__ __forceinline__ void grid_grad_3d(const float4* __restrict__ G, int n
                                              T& gx, T& gy, T& gz, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy, fz;
-  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy), iz = cell_of(z * s, n, fz);
+  const int ix = cell_of(x, s, n, fx), iy = cell_of(y, s, n, fy),
+            iz = cell_of(z, s, n, fz);
   if (!cell_in_table(err, ix, iy, iz, n)) {
     gx = gy = gz = T(0);
     return;
@@ -363,17 +387,17 @@ __device__ __forceinline__ void grid_grad_3d(const float4* __restrict__ G, int n
     for (int cy = 0; cy < 2; ++cy) {
       const float4* q = p + cz * nn + cy * n;
       const float4 a = __ldg(q), b = __ldg(q + 1);
-      acc[0][cy][cz] = (T)a.x + fx * ((T)b.x - (T)a.x);
-      acc[1][cy][cz] = (T)a.y + fx * ((T)b.y - (T)a.y);
-      acc[2][cy][cz] = (T)a.z + fx * ((T)b.z - (T)a.z);
+      acc[0][cy][cz] = fma_rn(fx, sub_rn((T)b.x, (T)a.x), (T)a.x);
+      acc[1][cy][cz] = fma_rn(fx, sub_rn((T)b.y, (T)a.y), (T)a.y);
+      acc[2][cy][cz] = fma_rn(fx, sub_rn((T)b.z, (T)a.z), (T)a.z);
     }
   }
   T out[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const T l0 = acc[c][0][0] + fy * (acc[c][1][0] - acc[c][0][0]);
-    const T l1 = acc[c][0][1] + fy * (acc[c][1][1] - acc[c][0][1]);
-    out[c] = l0 + fz * (l1 - l0);
+    const T l0 = fma_rn(fy, sub_rn(acc[c][1][0], acc[c][0][0]), acc[c][0][0]);
+    const T l1 = fma_rn(fy, sub_rn(acc[c][1][1], acc[c][0][1]), acc[c][0][1]);
+    out[c] = fma_rn(fz, sub_rn(l1, l0), l0);
   }
   gx = out[0];
   gy = out[1];
@@ -421,7 +445,7 @@ __device__ __forceinline__ void grid_cells_2d(const float4* __restrict__ C, int 
                                               T& gx, T& gy, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy;
-  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy);
+  const int ix = cell_of(x, s, n, fx), iy = cell_of(y, s, n, fy);
   if (!cell_in_table(err, ix, iy, 0, n)) {
     gx = gy = T(0);
     return;
@@ -429,18 +453,18 @@ __device__ __forceinline__ void grid_cells_2d(const float4* __restrict__ C, int 
   const float4* p = C + 2 * ((size_t)iy * (n - 1) + ix);
   float4 a, b;
   ldg_v8(p, a, b);
-  gx = (a.x + fx * a.y) + fy * (a.z + fx * a.w);
-  gy = (b.x + fx * b.y) + fy * (b.z + fx * b.w);
+  gx = fma_rn(fy, fma_rn(fx, (T)a.w, (T)a.z), fma_rn(fx, (T)a.y, (T)a.x));
+  gy = fma_rn(fy, fma_rn(fx, (T)b.w, (T)b.z), fma_rn(fx, (T)b.y, (T)b.x));
 }
 
 template <class T>
 __device__ __forceinline__ T cell_poly3(const float4 lo, const float4 hi, T fx, T fy, T fz) {
   // lo = (c000, c100, c010, c001), hi = (c110, c101, c011, c111)
-  const T a = lo.x + fz * lo.w;  // c000 + c001 fz
-  const T b = lo.z + fz * hi.z;  // c010 + c011 fz
-  const T c = lo.y + fz * hi.y;  // c100 + c101 fz
-  const T d = hi.x + fz * hi.w;  // c110 + c111 fz
-  return (a + fy * b) + fx * (c + fy * d);
+  const T a = fma_rn(fz, (T)lo.w, (T)lo.x);  // c000 + c001 fz
+  const T b = fma_rn(fz, (T)hi.z, (T)lo.z);  // c010 + c011 fz
+  const T c = fma_rn(fz, (T)hi.y, (T)lo.y);  // c100 + c101 fz
+  const T d = fma_rn(fz, (T)hi.w, (T)hi.x);  // c110 + c111 fz
+  return fma_rn(fx, fma_rn(fy, d, c), fma_rn(fy, b, a));
 }
 
 __device__ __forceinline__ float half_lo(float w) {
@@ -455,7 +479,8 @@ __device__ __forceinline__ void grid_cells_3d(const float4* __restrict__ C, int 
                                               T& gx, T& gy, T& gz, unsigned* err = nullptr) {
   const T s = (T)(n - 1);
   T fx, fy, fz;
-  const int ix = cell_of(x * s, n, fx), iy = cell_of(y * s, n, fy), iz = cell_of(z * s, n, fz);
+  const int ix = cell_of(x, s, n, fx), iy = cell_of(y, s, n, fy),
+            iz = cell_of(z, s, n, fz);
   if (!cell_in_table(err, ix, iy, iz, n)) {
     gx = gy = gz = T(0);
     return;
@@ -482,11 +507,13 @@ __device__ __forceinline__ void grid_cells_3d(const float4* __restrict__ C, int 
 // ---------------------------------------------------------------------------
 // Compensated (Kahan) summation for the FP32 Z and xi accumulators.
 // ---------------------------------------------------------------------------
+// The term enters as a product p * q, formed with the compensation's
+// subtraction in one rounding: y = p q - comp.
 template <class T>
-__device__ __forceinline__ void kahan_add(T& sum, T& comp, T term) {
-  const T y = term - comp;
-  const T t = sum + y;
-  comp = (t - sum) - y;
+__device__ __forceinline__ void kahan_add(T& sum, T& comp, T p, T q) {
+  const T y = fma_rn(p, q, -comp);
+  const T t = add_rn(sum, y);
+  comp = sub_rn(sub_rn(t, sum), y);
   sum = t;
 }
 

@@ -154,7 +154,7 @@ template <class P, class T, int D>
 __device__ __forceinline__ bool should_finish(const PathState<T>& s, T thr0) {
   const T m = (D == 3) ? face_distance(s.x[0], s.x[1], s.x[2]) : face_distance(s.x[0], s.x[1]);
   T thr = thr0;
-  if (P::kAniso || P::kIsoScaled) thr *= P::template exit_scale<T>(s.x[0], s.x[1], s.x[2]);
+  if (P::kAniso || P::kIsoScaled) thr = mul_rn(thr, P::template exit_scale<T>(s.x[0], s.x[1], s.x[2]));
   return m <= thr;
 }
 
@@ -205,11 +205,11 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
   T sdW[3];
   const T dW0 = dW[0], dW1 = dW[1];
   if (P::kAniso) {  // sigma = sqrt(a) [[1, 0], [1/2, sqrt(3)/2]]
-    sdW[0] = o.sa * dW0;
-    sdW[1] = o.sa * (T(0.5) * dW0 + T(0.86602540378443864676) * dW1);
+    sdW[0] = mul_rn(o.sa, dW0);
+    sdW[1] = mul_rn(o.sa, fma_rn(T(0.86602540378443864676), dW1, mul_rn(T(0.5), dW0)));
   } else if (P::kIsoScaled) {  // sigma = sa I
-    sdW[0] = o.sa * dW0;
-    sdW[1] = o.sa * dW1;
+    sdW[0] = mul_rn(o.sa, dW0);
+    sdW[1] = mul_rn(o.sa, dW1);
   } else {
     sdW[0] = dW0;
     sdW[1] = dW1;
@@ -221,15 +221,16 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
       gv[1] = o.g1;
       gv[2] = o.g2;
     }
-    T dot = gv[0] * sdW[0] + gv[1] * sdW[1];
-    if (D == 3) dot += gv[2] * sdW[2];
-    kahan_add(s.XI, s.XIc, -s.Y * dot);
+    T dot = fma_rn(gv[1], sdW[1], mul_rn(gv[0], sdW[0]));
+    if (D == 3) dot = fma_rn(gv[2], sdW[2], dot);
+    kahan_add(s.XI, s.XIc, -s.Y, dot);
   }
-  if (!P::kUnitY) kahan_add(s.Z, s.Zc, -h * s.Y * o.f);
-  s.x[0] += h * o.b0 + sdW[0];
-  s.x[1] += h * o.b1 + sdW[1];
-  if (D == 3) s.x[2] += h * o.b2 + sdW[2];
-  if (!P::kUnitY) s.Y *= (YRULE && a.y_exp) ? m_exp(-h * o.c) : (T(1) - h * o.c);
+  if (!P::kUnitY) kahan_add(s.Z, s.Zc, mul_rn(-h, s.Y), o.f);
+  s.x[0] = add_rn(s.x[0], fma_rn(h, o.b0, sdW[0]));
+  s.x[1] = add_rn(s.x[1], fma_rn(h, o.b1, sdW[1]));
+  if (D == 3) s.x[2] = add_rn(s.x[2], fma_rn(h, o.b2, sdW[2]));
+  if (!P::kUnitY)
+    s.Y = mul_rn(s.Y, (YRULE && a.y_exp) ? m_exp(mul_rn(-h, o.c)) : fma_rn(-h, o.c, T(1)));
   s.k += 1;
 }
 
@@ -332,8 +333,8 @@ __device__ __forceinline__ void score_path(const PathState<T>& s, T& phi, T& xi)
   T p[3] = {s.x[0], s.x[1], s.x[2]};
   project_box<T>(p, D);
   const T g = P::template g<T>(p[0], p[1], p[2]);
-  phi = g * s.Y + (s.Z - s.Zc);
-  xi = s.XI - s.XIc;
+  phi = fma_rn(g, s.Y, sub_rn(s.Z, s.Zc));
+  xi = sub_rn(s.XI, s.XIc);
 }
 
 // Exit scoring and the exact fixed-point accumulation into the node record.
@@ -492,6 +493,117 @@ __device__ __forceinline__ void init_lane(const PathArgs& a, PathState<T>& s, La
   load_seg<T, D>(a.seg[0], ls);
 }
 
+// One ordinary iteration: STEPS / 2 Philox blocks, two steps each; the exit
+// test precedes every step.  `fin` / `trunc` report a path that ended.
+template <class P, class T, int CV, bool MULTI, int STEPS>
+__device__ __forceinline__ void iteration_2d(const PathArgs& a, PathState<T>& s,
+                                             const LaneSeg<T>& ls, bool active, bool& fin,
+                                             bool& trunc) {
+#pragma unroll
+  for (int half = 0; half < STEPS / 2; ++half) {
+    uint4 w = make_uint4(0, 0, 0, 0);
+    if (active && !fin) fin = should_finish<P, T, 2>(s, ls.thr0);
+    if (active && !fin) {
+      w = path_block<MULTI>(a, s.seg, (uint32_t)(s.k >> 1), s.path, s.node);
+      T n[3];
+      box_muller(w.x, w.y, n[0], n[1], ls.sqh);
+      n[2] = T(0);
+      euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
+    }
+    if (active && !fin) fin = should_finish<P, T, 2>(s, ls.thr0);
+    if (active && !fin) {
+      T n[3];
+      box_muller(w.z, w.w, n[0], n[1], ls.sqh);
+      n[2] = T(0);
+      euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
+    }
+  }
+}
+
+// Drain iterations.  Once the launch's cursor is exhausted a warp only
+// finishes the paths it holds; as lanes retire, the launch's time becomes the
+// serial latency of its longest paths, and a lone path spends most of each
+// step drawing its random numbers (Philox rounds, Box-Muller), which do not
+// depend on the path's state.  When at most half the lanes of a warp still
+// run a path, the idle lanes draw them: with A running lanes, every lane L
+// computes Philox block m = L / A of running lane L mod A (counted from that
+// lane's current block) and its four normals, and the running lanes then take
+// 2 * floor(32 / A) steps reading their normals from the helpers with warp
+// shuffles.  The values are the ones a lane would draw itself (same key,
+// same counter, same arithmetic), so results do not change.
+#ifndef PDD_TAIL_COOP
+#define PDD_TAIL_COOP 1
+#endif
+
+// Position of the q-th (from 0) set bit of m, q < popc(m): the largest p
+// with fewer than q + 1 set bits below it, by binary search.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int q) {
+  int p = 0;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1)
+    if (__popc(m & ((1u << (p + w)) - 1u)) <= q) p += w;
+  return p;
+}
+
+// Helper side: this lane's Philox block (block blk + m, m = lane / A, of
+// running lane lane % A, whose current block counter is `blk`) as four scaled
+// normals; lanes with lane / A >= blocks draw none.
+template <class T, bool MULTI>
+__device__ __forceinline__ void coop_draw(const PathArgs& a, const PathState<T>& s,
+                                          const LaneSeg<T>& ls, unsigned runm, int blocks,
+                                          uint32_t blk, T (&nv)[4]) {
+  const int lane = (int)(threadIdx.x & 31u), A = __popc(runm);
+  const int q = lane % A, m = lane / A;
+  const int owner = nth_set_bit(runm, q);
+  const uint32_t o_seg = __shfl_sync(kFull, s.seg, owner);
+  const uint32_t o_path = __shfl_sync(kFull, s.path, owner);
+  const uint32_t o_node = __shfl_sync(kFull, s.node, owner);
+  const uint32_t o_blk = __shfl_sync(kFull, blk, owner);
+  const T o_sqh = __shfl_sync(kFull, ls.sqh, owner);
+  nv[0] = nv[1] = nv[2] = nv[3] = T(0);
+  if (m < blocks) {
+    const uint4 w = path_block<MULTI>(a, o_seg, o_blk + (uint32_t)m, o_path, o_node);
+    box_muller(w.x, w.y, nv[0], nv[1], o_sqh);
+    box_muller(w.z, w.w, nv[2], nv[3], o_sqh);
+  }
+}
+
+// 2D: block m of a running lane feeds its steps 2m and 2m + 1 (normals 4m ..
+// 4m + 3), so the lane's counter at the iteration start is even.
+template <class P, class T, int CV, bool MULTI>
+__device__ __forceinline__ void coop_iteration_2d(const PathArgs& a, PathState<T>& s,
+                                                  const LaneSeg<T>& ls, bool active,
+                                                  unsigned runm, bool& fin, bool& trunc) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int A = __popc(runm), blocks = 32 / A;
+  T nv[4];
+  coop_draw<T, MULTI>(a, s, ls, runm, blocks, (uint32_t)s.k >> 1, nv);
+  const int r = __popc(runm & ((1u << lane) - 1u));  // rank among running lanes
+  bool run = active;
+  for (int m = 0; m < blocks; ++m) {
+    const int src = (r + A * m) & 31;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      T n[3];
+      n[0] = __shfl_sync(kFull, nv[2 * h2], src);
+      n[1] = __shfl_sync(kFull, nv[2 * h2 + 1], src);
+      n[2] = T(0);
+      if (run) run = !should_finish<P, T, 2>(s, ls.thr0);
+      if (run) {
+        euler_step<P, T, 2, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) {
+          trunc = true;
+          run = false;
+        }
+      }
+    }
+    if (__ballot_sync(kFull, run) == 0u) break;
+  }
+  fin = active && !run;
+}
+
 // The segment-table build keeps per-lane segment parameters in registers; at
 // 65 registers a 512-thread block rounds up to 72 per thread and only one
 // block fits an SM, so it is capped at 64 (two blocks), which measured faster
@@ -509,9 +621,10 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (MULTI && sizeof(T) == 4) ? 
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
   while (refill<T, 2, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
+    if (PDD_TAIL_COOP && exhausted) break;  // warp-uniform: on to the drain
     bool fin = false, trunc = false;
-    // STEPS / 2 Philox blocks per iteration, two steps each; the exit test
-    // precedes every step
+    // the body of iteration_2d, written out: inlining the function here
+    // changes the compiler's schedule of this loop (measured slower)
 #pragma unroll
     for (int half = 0; half < STEPS / 2; ++half) {
       uint4 w = make_uint4(0, 0, 0, 0);
@@ -536,6 +649,15 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (MULTI && sizeof(T) == 4) ? 
     ring_exit<P, T, 2, MULTI>(a, ring, rc, s, active && fin, trunc);
     if (fin) active = false;
   }
+  // drain: the cursor is exhausted and the warp finishes the paths it holds
+  while (PDD_TAIL_COOP && exhausted) {
+    const unsigned runm = __ballot_sync(kFull, active);
+    if (runm == 0u) break;
+    bool fin = false, trunc = false;
+    coop_iteration_2d<P, T, CV, MULTI>(a, s, ls, active, runm, fin, trunc);
+    ring_exit<P, T, 2, MULTI>(a, ring, rc, s, active && fin, trunc);
+    if (fin) active = false;
+  }
   if (rc.held > 0u) ring_drain<P, T, 2, MULTI>(a, ring, rc.head - rc.held, rc.held);
   cache_flush(a);
 }
@@ -545,6 +667,97 @@ __global__ void __launch_bounds__(kMaxBlockThreads, (MULTI && sizeof(T) == 4) ? 
 //   step 0: a0 a1 a2   step 1: a3 b0 b1   step 2: b2 b3 c0   step 3: c1 c2 c3
 // Blocks are drawn only when the path is still running.  STEPS / 4 such
 // groups of four steps run per iteration (between lane refills).
+// One ordinary 3D iteration runs STEPS / 4 such groups; the exit test
+// precedes every step.
+template <class P, class T, int CV, bool MULTI, int STEPS>
+__device__ __forceinline__ void iteration_3d(const PathArgs& a, PathState<T>& s,
+                                             const LaneSeg<T>& ls, bool active, bool& fin,
+                                             bool& trunc) {
+#pragma unroll
+  for (int quad = 0; quad < STEPS / 4; ++quad) {
+    T carry0 = T(0), carry1 = T(0);  // normals left over from the previous block
+    uint4 w = make_uint4(0, 0, 0, 0);
+    const uint32_t blk0 = 3u * ((uint32_t)s.k >> 2);
+    // step 0
+    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+    if (active && !fin) {
+      w = path_block<MULTI>(a, s.seg, blk0, s.path, s.node);
+      T n[3], n3;
+      box_muller(w.x, w.y, n[0], n[1], ls.sqh);
+      box_muller(w.z, w.w, n[2], n3, ls.sqh);
+      carry0 = n3;
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
+    }
+    // step 1
+    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+    if (active && !fin) {
+      w = path_block<MULTI>(a, s.seg, blk0 + 1u, s.path, s.node);
+      T n[3];
+      n[0] = carry0;
+      box_muller(w.x, w.y, n[1], n[2], ls.sqh);
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
+    }
+    // step 2
+    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+    if (active && !fin) {
+      T n[3];
+      box_muller(w.z, w.w, n[0], n[1], ls.sqh);
+      w = path_block<MULTI>(a, s.seg, blk0 + 2u, s.path, s.node);
+      box_muller(w.x, w.y, n[2], carry1, ls.sqh);
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
+    }
+    // step 3
+    if (active && !fin) fin = should_finish<P, T, 3>(s, ls.thr0);
+    if (active && !fin) {
+      T n[3];
+      n[0] = carry1;
+      box_muller(w.z, w.w, n[1], n[2], ls.sqh);
+      euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+      if (s.k >= ls.max_steps) fin = trunc = true;
+    }
+  }
+}
+
+// The 3D drain iteration: a running lane's block counter at the iteration
+// start is 3 k / 4 (k a multiple of four); with A <= 10 running lanes each
+// takes 4 * floor(floor(32 / A) / 3) steps, normal i of a group of four steps
+// coming from helper block i / 4 of that group, word i mod 4.
+template <class P, class T, int CV, bool MULTI>
+__device__ __forceinline__ void coop_iteration_3d(const PathArgs& a, PathState<T>& s,
+                                                  const LaneSeg<T>& ls, bool active,
+                                                  unsigned runm, bool& fin, bool& trunc) {
+  const unsigned lane = threadIdx.x & 31u;
+  const int A = __popc(runm), quads = (32 / A) / 3;
+  T nv[4];
+  coop_draw<T, MULTI>(a, s, ls, runm, 3 * quads, 3u * ((uint32_t)s.k >> 2), nv);
+  const int r = __popc(runm & ((1u << lane) - 1u));
+  bool run = active;
+  for (int j = 0; j < quads; ++j) {
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      T n[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const int i = 3 * st + c;  // normal index within the group of four steps
+        n[c] = __shfl_sync(kFull, nv[i & 3], (r + A * (3 * j + (i >> 2))) & 31);
+      }
+      if (run) run = !should_finish<P, T, 3>(s, ls.thr0);
+      if (run) {
+        euler_step<P, T, 3, CV, MULTI>(a, s, ls, n);
+        if (s.k >= ls.max_steps) {
+          trunc = true;
+          run = false;
+        }
+      }
+    }
+    if (__ballot_sync(kFull, run) == 0u) break;
+  }
+  fin = active && !run;
+}
+
 template <class P, class T, int CV, bool MULTI, int STEPS>
 __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
     paths_3d(const __grid_constant__ PathArgs a) {
@@ -556,8 +769,14 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
   RingCursor rc;
   bool active = false, exhausted = false;
   unsigned long long bnext = 0, bend = 0;
+  // The ordinary iterations run until the cursor is exhausted and at most
+  // ten lanes of the warp still run a path (warp-uniform); then drain
+  // iterations alternate with the check.
+  for (;;) {
   while (refill<T, 3, MULTI>(a, s, ls, active, bnext, bend, exhausted)) {
+    if (PDD_TAIL_COOP && exhausted && __popc(__ballot_sync(kFull, active)) <= 10) break;
     bool fin = false, trunc = false;
+    // the body of iteration_3d, written out (as in paths_2d)
 #pragma unroll
     for (int quad = 0; quad < STEPS / 4; ++quad) {
       T carry0 = T(0), carry1 = T(0);  // normals left over from the previous block
@@ -606,6 +825,13 @@ __global__ void __launch_bounds__(kMaxBlockThreads, PDD_MIN_BLOCKS_3D)
     }
     ring_exit<P, T, 3, MULTI>(a, ring, rc, s, active && fin, trunc);
     if (fin) active = false;
+  }
+  const unsigned runm = __ballot_sync(kFull, active);
+  if (!PDD_TAIL_COOP || runm == 0u) break;
+  bool fin = false, trunc = false;
+  coop_iteration_3d<P, T, CV, MULTI>(a, s, ls, active, runm, fin, trunc);
+  ring_exit<P, T, 3, MULTI>(a, ring, rc, s, active && fin, trunc);
+  if (fin) active = false;
   }
   if (rc.held > 0u) ring_drain<P, T, 3, MULTI>(a, ring, rc.head - rc.held, rc.held);
   cache_flush(a);
