@@ -49,15 +49,15 @@ TARGET_RMSE = 1e-3
 # smsp__thread_inst_executed.sum over the path-steps of the full-size launches
 # of this benchmark (a one-pass capture of the 4-steps-per-iteration kernels;
 # the planning estimates were 110 and 150).
-ALGO_INSTR = {"plain": 104.5, "cv": 134.2}
+ALGO_INSTR = {"plain": 104.5, "cv": 134.4}
 # DRAM bytes (read + write) per launch of the dominant kernel (the eps = 1e-2
 # pass) from the same full-size capture; None whenever the kernel has changed
 # since that capture.
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES = 1275136
 # Thread-instructions per path-step of the 3D control-variate kernel over the
 # full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
 # over its path-steps, a one-pass capture; the planning estimate was 190).
-INSTR_3D = 223.6
+INSTR_3D = 223.1
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
@@ -78,14 +78,15 @@ def parse_args():
                     help="profiling case: the 256 nodes x 1e4 paths (same kernels, launch "
                          "shape and passes as the default step)")
     ap.add_argument("--workload", choices=["c0", "c1", "c2", "c3", "c4", "fit", "mlmc", "paper",
-                                           "peaks", "cascade"],
+                                           "peaks", "cascade", "cascade3d"],
                     default="c1",
                     help="c1 (default): 2D, 256 nodes, plain + 3 control grids; c0: 24 nodes, "
                          "plain, dt 1e-3; fit: Algorithm 3 on the 24 nodes; c2: 3D "
                          "three-level cascade in one launch (CUDA graph); c3: serving with "
                          "Poisson arrivals; c4: anisotropic 2D, FP32 vs FP64 paths; mlmc: "
                          "multilevel driver at a fixed RMSE vs the single level; paper: the "
-                         "paper's example PDE on 18 nodes")
+                         "paper's example PDE on 18 nodes; cascade / cascade3d: Algorithms 3-5 "
+                         "on the 2D / 3D nodes")
     ap.add_argument("--a0", type=float, default=1e-3, help="cascade: nodal target tolerance")
     ap.add_argument("--window", type=float, default=10.0, help="c3: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="c3: arrivals per second")
@@ -1075,10 +1076,11 @@ def run_fit(args):
 
 def run_cascade(args):
     """The cascade Algorithm 4 schedules, run (Algorithm 5's nodal loop) on
-    the 256 interfacial nodes of the 2D problem: Algorithm 3 fit (100 time
-    steps in [1e-3, 1e-2], 10^4 paths each, psi from w = sin 3pi x sin 2pi y;
-    nodes within the shrinkage layer at some h of the cloud cannot be fitted
-    and are left out),
+    the 256 interfacial nodes of the 2D problem (--workload cascade) or on
+    every 16th of the 9,216 nodes of the 3D problem (--workload cascade3d, 576
+    nodes, 65^3 grids): Algorithm 3 fit (100 time steps in [1e-3, 1e-2], 10^4
+    paths each, psi from w = sin 3pi x sin 2pi y [sin pi z]; nodes within the
+    shrinkage layer at some h of the cloud cannot be fitted and are left out),
     kappa measured, the schedule from a0, every level's balanced (h, N) per
     node, all levels in one launch; against PlainPDD(a0) run the same way.
     The previous iterate of tolerance a is synthetic, v = u + (a/2) w."""
@@ -1088,21 +1090,25 @@ def run_cascade(args):
     from paper_1512_02818_gb300 import cascade as C
     from paper_1512_02818_gb300 import pdd
     from paper_1512_02818_gb300 import workloads as W
+    three_d = args.workload == "cascade3d"
+    kind = pdd.PDD_PROBLEM_CUBE_3D if three_d else pdd.PDD_PROBLEM_CFG0_2D
+    gn = 65 if three_d else GRID_N
     ctx = pdd.Context(0)
     torch.cuda.set_stream(ctx.stream)
-    prob = pdd.Problem(ctx, pdd.PDD_PROBLEM_CFG0_2D)
+    prob = pdd.Problem(ctx, kind)
     w_slot = 7
-    w = W.control_grid(0, GRID_N, 1.0) - W.control_grid(0, GRID_N, 0.0)
+    w = W.control_grid(kind, gn, 1.0) - W.control_grid(kind, gn, 0.0)
     prob.set_control_grid(w_slot, w)
-    nodes = W.workload_nodes("c1")
-    u = W.exact_u(0, nodes.astype(np.float64))
+    nodes = W.workload_nodes("c2")[::16] if three_d else W.workload_nodes("c1")
+    dim = nodes.shape[1]
+    u = W.exact_u(kind, nodes.astype(np.float64))
     n_fit = 10_000
     t0 = time.perf_counter()
     fit = prob.fit_constants(nodes, n_fit, 1e-3, 1e-2, 100, grid_id=w_slot, stream_tag_base=200)
     fit_s = time.perf_counter() - t0
     fit_steps = float((fit["cloud"][:, :, 3] / fit["cloud"][:, :, 0]).sum() * n_fit)
     # kappa: per-step time of the control-variate and plain kernels on these nodes
-    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).cuda() for j in range(2)]
+    cols = [torch.from_numpy(np.ascontiguousarray(nodes[:, j])).cuda() for j in range(dim)]
     rate = {}
     for name, gid in (("plain", pdd.PDD_CV_NONE), ("cv", w_slot)):
         prob.estimate(cols, 20000, 1e-3, grid_id=gid)
@@ -1120,7 +1126,7 @@ def run_cascade(args):
     a, sp = pdd.pdd_schedule(fit["K"], fit["beta"], fit["alpha"], fit["V_phi"], fit["V_psi"],
                              fit["rho_phi_psi"], 1.0, kappa, a0, max_levels=6)
     for j in range(len(a) - 1):  # level j reads the iterate of tolerance a[j+1]
-        prob.set_control_grid(j, W.control_grid(0, GRID_N, a[j + 1] / 2.0))
+        prob.set_control_grid(j, W.control_grid(kind, gn, a[j + 1] / 2.0))
     levels = C.plan_levels(fit, a)
     C.run_levels(prob, nodes, C.plan_levels(fit, a), n_pilot=200)  # warm-up (kernel loads)
     run = C.run_levels(prob, nodes, levels)
@@ -1129,12 +1135,15 @@ def run_cascade(args):
     C.run_levels(prob, nodes, C.plan_levels(fit, [a0]), n_pilot=200, n_max=1000)  # warm-up
     plain = C.run_levels(prob, nodes, plain_lv)
     plain_obs = plain["levels"][0]["path_steps"]
-    out = {"workload": "cascade", "metric": METRIC, "unit": UNIT, "dtype": "f32",
+    where = ("576 nodes (every 16th) of the 3D problem, previous iterates v = u + (a_{j+1}/2) "
+             "sin 3pi x sin 2pi y sin pi z on 65^3" if three_d else
+             "256 nodes of the 2D problem, previous iterates v = u + (a_{j+1}/2) sin 3pi x "
+             "sin 2pi y on 129^2")
+    out = {"workload": args.workload, "metric": METRIC, "unit": UNIT, "dtype": "f32",
            "data": "synthetic",
            "value": (sum(o["path_steps"] for o in run["levels"])) / run["wall_s"],
            "config": {"workload": "Algorithm 4 schedule run as one launch (Algorithm 5 nodal "
-                                  "loop), 256 nodes of the 2D problem, target a0; previous "
-                                  "iterates v = u + (a_{j+1}/2) sin 3pi x sin 2pi y on 129^2",
+                                  "loop), " + where + ", target a0",
                       "a0": a0, "q": 2.0, "delta": 1.0, "fit_paths_per_h": n_fit,
                       "fit_time_steps": 100, "nodes_fitted": int(ok.sum()),
                       "nodes_left_out": int((~ok).sum())},
@@ -1246,7 +1255,8 @@ def main():
         if rank == 0:
             fn = {"c0": run_c0, "c2": run_c2, "c3": run_c3, "c4": run_c4,
                   "fit": run_fit, "mlmc": run_mlmc, "paper": run_paper,
-                  "peaks": run_peaks, "cascade": run_cascade}[args.workload]
+                  "peaks": run_peaks, "cascade": run_cascade,
+                  "cascade3d": run_cascade}[args.workload]
             print(json.dumps(fn(args)), flush=True)
         return
     if args.impl == "reference":

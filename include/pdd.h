@@ -511,9 +511,11 @@ typedef struct {
                                   (PDD_ERR_DEADLINE) a request whose predicted path-steps,
                                   added to the predicted remaining path-steps of every
                                   queued and running request, would take longer than
-                                  deadline_s at the server's measured rate (a guarantee under
-                                  PDD_SERVE_EARLIEST_DEADLINE, an estimate under the other
-                                  policies); 0: no deadline */
+                                  0.9 x deadline_s at the server's measured rate (the rest
+                                  is a margin for the error of the predicted work and rate;
+                                  a guarantee under PDD_SERVE_EARLIEST_DEADLINE as far as the
+                                  predictions hold, an estimate under the other policies);
+                                  0: no deadline */
   double rate_hint;            /* path-steps/s assumed until the server has measured its own
                                   rate over retired launches (0: 1e11) */
 } pdd_server_desc;

@@ -21,8 +21,8 @@
 // pilot launch the first time the pair is seen and refined by every
 // completed request; with a deadline set, pdd_submit refuses a request whose
 // work, after the predicted remaining work of everything queued and running,
-// would not finish within the deadline at the measured rate (path-steps of
-// retired launches over the time they took).  Under the earliest-deadline
+// would not finish within 90 % of the deadline at the measured rate
+// (path-steps of retired launches over the time they took).  Under the earliest-deadline
 // policy (every request has the same relative deadline, so it serves them in
 // submission order) the admitted work finishes in time as far as the
 // prediction holds, and no executed work is thrown away under overload;
@@ -250,6 +250,12 @@ double backlog_work(pdd_server* s) {
   }
   return b;
 }
+
+// Share of the deadline that admission fills with predicted work; the rest
+// is a margin for the error of the predicted work and rate (exit-index
+// estimates from a pilot, the measured rate's drift with the request mix,
+// host gaps between launches).
+constexpr double kDeadlineShare = 0.9;
 
 // Path-steps per second of GPU-busy time over every retired launch (launch
 // overheads and the drain of small launches included), once 0.2 s of busy
@@ -810,7 +816,7 @@ int pdd_submit(pdd_server* s, pdd_problem* p, const pdd_estimate_args* a, uint64
     const double work = (double)r->n_nodes * (double)r->n_paths * r->est_steps;
     const double backlog = backlog_work(s);
     const double rate = current_rate(s);
-    if ((backlog + work) / rate > s->desc.deadline_s) {
+    if ((backlog + work) / rate > kDeadlineShare * s->desc.deadline_s) {
       s->st.rejected_deadline++;
       set_error("pdd_submit: predicted %.3g path-steps after a backlog of %.3g do not finish "
                 "within the %.3g s deadline at %.3g path-steps/s",
