@@ -1129,11 +1129,11 @@ def run_cascade(args):
         prob.set_control_grid(j, W.control_grid(kind, gn, a[j + 1] / 2.0))
     levels = C.plan_levels(fit, a)
     C.run_levels(prob, nodes, C.plan_levels(fit, a), n_pilot=200)  # warm-up (kernel loads)
-    run = C.run_levels(prob, nodes, levels)
+    run = C.run_levels(prob, nodes, levels, e_tau=fit["E_tau"])
     summ = C.summary(levels, run, u, kappa, fit, a0)
     plain_lv = C.plan_levels(fit, [a0])
     C.run_levels(prob, nodes, C.plan_levels(fit, [a0]), n_pilot=200, n_max=1000)  # warm-up
-    plain = C.run_levels(prob, nodes, plain_lv)
+    plain = C.run_levels(prob, nodes, plain_lv, e_tau=fit["E_tau"])
     plain_obs = plain["levels"][0]["path_steps"]
     where = ("576 nodes (every 16th) of the 3D problem, previous iterates v = u + (a_{j+1}/2) "
              "sin 3pi x sin 2pi y sin pi z on 65^3" if three_d else

@@ -16,10 +16,11 @@ the caller loaded into slot j, standing in for the iterate of tolerance
 a_{j+1}.
 
 Levels share one launch.  A launch holds at most 128 segments, and a segment
-has one time step and one path count, so each level's nodes are sorted by
-their planned time step and cut into contiguous groups; a group runs at the
-smallest h and the largest N of its nodes (both stay within the tolerance),
-on a random stream of its own.  The path count of a controlled level needs
+has one time step and one path count, so each level's nodes are cut into
+contiguous groups, sorted by their planned time step for the pilot and, once
+every node's N is known, by whichever of h or the per-node cost N E[tau] / h
+predicts the cheaper launch; a group runs at the smallest h and the largest N
+of its nodes (both stay within the tolerance), on a random stream of its own.  The path count of a controlled level needs
 V[phi + xi] at that level's h, which only a run can give: a pilot launch of
 `n_pilot` paths per node measures every level's variances first (its cost is
 reported apart).
@@ -46,10 +47,66 @@ def fitted_subset(fit, nodes):
     return ok, {k: np.asarray(fit[k])[ok] for k in FIT_KEYS}, np.asarray(nodes)[ok]
 
 
-def group_nodes(h, groups):
-    """Contiguous groups of node indices sorted by h (at most `groups`)."""
-    order = np.argsort(np.asarray(h), kind="stable")
+def group_nodes(key, groups):
+    """Contiguous groups of node indices sorted by `key` (at most `groups`)."""
+    order = np.argsort(np.asarray(key), kind="stable")
     return [g for g in np.array_split(order, max(1, min(groups, order.size))) if g.size]
+
+
+def grouped_cost(groups, h, n_paths, e_tau):
+    """Predicted path-steps of a level run as `groups` (each group at the
+    smallest h and the largest N of its nodes): sum over nodes of
+    N_group E[tau_i] / h_group."""
+    return float(sum(np.max(n_paths[g]) * np.sum(e_tau[g]) / np.min(h[g]) for g in groups))
+
+
+def partition(order, h, n_paths, e_tau, groups):
+    """Cut the nodes, taken in `order`, into at most `groups` contiguous
+    groups of least grouped_cost (dynamic programming over the cut points:
+    best[k][j] = min over i of best[k-1][i] + cost of nodes i..j-1)."""
+    hh, nn, ee = h[order], n_paths[order], e_tau[order]
+    n = order.size
+    groups = max(1, min(groups, n))
+    ce = np.concatenate([[0.0], np.cumsum(ee)])
+    # cost[i, j] of the group order[i:j] (j > i): max N, min h over the range
+    cost = np.full((n + 1, n + 1), np.inf)
+    for i in range(n):
+        mx = np.maximum.accumulate(nn[i:])
+        mn = np.minimum.accumulate(hh[i:])
+        cost[i, i + 1:] = mx * (ce[i + 1:] - ce[i]) / mn
+    best = np.full(n + 1, np.inf)
+    best[0] = 0.0
+    cut = np.zeros((groups + 1, n + 1), dtype=np.int64)
+    for k in range(1, groups + 1):
+        tot = best[:, None] + cost  # [i, j]: best with k-1 groups up to i, then i..j-1
+        arg = np.argmin(tot, axis=0)
+        new_best = tot[arg, np.arange(n + 1)]
+        cut[k] = arg
+        best = np.minimum(best, new_best) if k > 1 else new_best
+        cut[k] = np.where(new_best <= best, arg, -1)
+    # walk back: at each k the cut that reached j (fewer groups when they tie)
+    out, j, k = [], n, groups
+    while j > 0:
+        while k > 0 and cut[k, j] < 0:
+            k -= 1
+        i = int(cut[k, j])
+        out.append(order[i:j])
+        j, k = i, k - 1
+    return out[::-1]
+
+
+def regroup(h, n_paths, e_tau, groups, dp_max_nodes=2048):
+    """The cheapest grouping of one level's nodes by predicted cost
+    (grouped_cost): contiguous groups of the nodes in order of h (the time
+    step) or of N (the path count), cut by dynamic programming (O(n^2) memory
+    and O(n^2 groups) time: equal-size groups above dp_max_nodes nodes)."""
+    if h.size > dp_max_nodes:
+        cands = [group_nodes(h, groups), group_nodes(n_paths, groups)]
+    else:
+        cands = [partition(np.argsort(h, kind="stable"), h, n_paths, e_tau, groups),
+                 partition(np.argsort(n_paths, kind="stable"), h, n_paths, e_tau, groups)]
+    costs = [grouped_cost(g, h, n_paths, e_tau) for g in cands]
+    return cands[int(np.argmin(costs))], min(costs)
 
 
 def plan_levels(fit, a, q=2.0, delta=1.0, h_min=1e-5, h_max=1e-2, max_segments=128):
@@ -89,9 +146,11 @@ def _segments(prob, cols_of, levels, n_paths_of, seed, tag_base, emit=False):
 
 
 def run_levels(prob, nodes, levels, q=2.0, n_pilot=2000, seed=1234, tag_base=4096,
-               n_max=(1 << 32) - 1, emit=False):
+               n_max=(1 << 32) - 1, emit=False, e_tau=None):
     """Pilot, then all levels in one launch.  Returns per-level observations
-    and the wall time of the main launch.  `nodes`: (n, D) float32 array."""
+    and the wall time of the main launch.  `nodes`: (n, D) float32 array;
+    `e_tau`: per-node expected exit times (Algorithm 3's), which weigh the
+    regrouping of each level by predicted cost (equal weights without)."""
     import torch
     dev = torch.device("cuda", prob.ctx.device)
     nodes = np.ascontiguousarray(nodes, dtype=np.float32)
@@ -117,10 +176,15 @@ def run_levels(prob, nodes, levels, q=2.0, n_pilot=2000, seed=1234, tag_base=409
         key = "var_cv" if lv["controlled"] else "var_phi"
         var[lv["j"]][idx] = res[key].cpu().numpy()
         pilot_steps += float(res["mean_steps"].cpu().numpy().sum()) * n_paths
+    e_tau = np.asarray(e_tau if e_tau is not None else np.ones(n), dtype=np.float64)
     for lv in levels:
         _, N = pdd.pdd_balanced_plan(lv["a"], np.zeros(n), var[lv["j"]], q=q, n_max=n_max)
         lv["n_paths"] = N
         lv["pilot_var"] = var[lv["j"]]
+        # with every node's N known, group the main launch by predicted cost
+        per_node = float(np.sum(N * e_tau / lv["h"]))
+        lv["groups"], grouped = regroup(lv["h"], N.astype(np.float64), e_tau, len(lv["groups"]))
+        lv["grouping_inflation"] = grouped / per_node if per_node > 0 else 1.0
     main = _segments(prob, cols_of, levels, lambda lv, idx: lv["n_paths"][idx].max(), seed,
                      tag_base, emit=emit)
     torch.cuda.synchronize()
@@ -175,6 +239,7 @@ def summary(levels, run, u, kappa, fit, a0, delta=1.0):
             "obs_mean_abs_rho": float(np.mean(np.abs(ob["rho"]))) if lv["controlled"] else None,
             "rmse_vs_exact": float(np.sqrt(np.mean((ob["estimate"] - u) ** 2))),
             "max_se_over_half_tolerance": float(np.max(2.0 * ob["se"] / lv["a"])),
+            "grouping_inflation": float(lv.get("grouping_inflation", 1.0)),
         })
         tot_pred += k * pred
         tot_obs += k * ob["path_steps"]

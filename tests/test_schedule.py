@@ -131,6 +131,42 @@ def test_cascade_plan_groups_partition_the_nodes():
         assert np.all(lv["pred_path_steps"] > 0)
 
 
+def test_cascade_regroup_is_the_cheapest_contiguous_cut():
+    """After the pilot every node of a level has its N; the main launch cuts
+    the nodes, in order of h or of N, into contiguous groups of least
+    predicted cost (each group at its smallest h and largest N).  Brute force
+    over every cut of tiny levels finds no cheaper grouping, and the groups
+    partition the nodes."""
+    import itertools
+
+    from paper_1512_02818_gb300 import cascade as C
+    rng = np.random.default_rng(5)
+    for n, k in ((1, 3), (4, 2), (6, 3), (7, 4), (8, 8)):
+        h = rng.uniform(1e-4, 1e-2, n)
+        N = np.ceil(rng.lognormal(8.0, 1.0, n))
+        e = rng.uniform(0.02, 0.2, n)
+        groups, cost = C.regroup(h, N, e, k)
+        assert np.array_equal(np.sort(np.concatenate(groups)), np.arange(n))
+        assert len(groups) <= k
+        assert np.isclose(C.grouped_cost(groups, h, N, e), cost, rtol=1e-12)
+        best = np.inf
+        for key in (h, N):
+            order = np.argsort(key, kind="stable")
+            for m in range(1, min(k, n) + 1):
+                for cuts in itertools.combinations(range(1, n), m - 1):
+                    bounds = (0,) + cuts + (n,)
+                    gs = [order[bounds[i]:bounds[i + 1]] for i in range(m)]
+                    best = min(best, C.grouped_cost(gs, h, N, e))
+        assert cost <= best * (1 + 1e-12)
+        assert cost >= best * (1 - 1e-12)
+    # one group per node when there are enough segments: no inflation
+    h = rng.uniform(1e-4, 1e-2, 5)
+    N = rng.uniform(10, 1e4, 5)
+    e = rng.uniform(0.02, 0.2, 5)
+    groups, cost = C.regroup(h, N, e, 8)
+    assert np.isclose(cost, np.sum(N * e / h), rtol=1e-12)
+
+
 def test_unfit_nodes_are_left_out(oracle_mod):
     """A node with NaN constants (Algorithm 3 could not fit it) does not change
     the schedule: library and oracle give the sequence of the other nodes."""
