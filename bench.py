@@ -395,6 +395,7 @@ def run_ours(args, rank, world, local):
     if not args.no_autotune:
         tuned = prob.autotune(cols_dev, n_paths, DT, grid_id=1)
     launch_iter = ctx.get_launch()[2]
+    launch_claim = ctx.get_claim()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -509,6 +510,7 @@ def run_ours(args, rank, world, local):
         "launch_shape": {"block_threads": tuned[0] or (512 if n_nodes <= 512 else 128),
                          "max_blocks": tuned[1],
                          "iteration": ["auto", "short", "long"][launch_iter],
+                         "paths_per_lane_claim": launch_claim or "auto",
                          "chosen_by": "pdd_autotune on the eps=1e-2 pass" if tuned[2]
                          else "library default"},
     }
@@ -645,6 +647,8 @@ def run_c2(args):
                        "l2": "flushed between steps (256 MB)"},
             "nodes_per_s": len(nodes) * args.steps / (total_ms / 1e3),
             "launch_shape": {"block_threads": tuned[0] or 128, "max_blocks": tuned[1],
+                             "iteration": ["auto", "short", "long"][ctx.get_launch()[2]],
+                             "paths_per_lane_claim": ctx.get_claim() or "auto",
                              "chosen_by": "pdd_autotune on 1/8 of the finest level" if tuned[2]
                              else "library default"},
             "levels": per_level, "graph_captures": ctx.graph_count(),

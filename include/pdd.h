@@ -226,6 +226,20 @@ int pdd_ctx_set_launch(pdd_ctx* ctx, int block_threads, int max_blocks);
 #define PDD_ITER_LONG 2
 int pdd_ctx_set_iteration(pdd_ctx* ctx, int mode);
 int pdd_ctx_get_launch(pdd_ctx* ctx, int* block_threads, int* max_blocks, int* iteration);
+/* Paths per lane a warp claims from a launch's path cursor at once (one
+   atomic per 32 x paths_per_lane consecutive path indices; the warp's lanes
+   then run them one at a time as they finish): 0 (the default) = automatic,
+   4 when the launch's paths are short (the segments with time steps of at
+   most 2e-3 hold at most 5 % of its expected path-steps) and it has at least
+   4 x 32 paths for every warp that can be resident, 1 otherwise; or a power
+   of two in [1, 64].  Larger claims hit the
+   cursor less often (it matters for paths of ~10 steps) but leave more
+   unstarted paths with one warp at the end of a launch.  Like the launch
+   shape, the claim changes only the speed.  PDD_ERR_INVALID for other values.
+   pdd_autotune searches it (1, 4, 16 against automatic).
+   pdd_ctx_get_claim reads the setting (0 = automatic).                       */
+int pdd_ctx_set_claim(pdd_ctx* ctx, int paths_per_lane);
+int pdd_ctx_get_claim(pdd_ctx* ctx, int* paths_per_lane);
 /* Stops the work in flight on the context (no counterpart in the paper):
    callable from any thread, also while another thread waits inside an
    estimate on this context.  The kernels take no further paths (a copy on a
@@ -470,12 +484,13 @@ int pdd_schedule_predict(const pdd_schedule_args* s, double a, double aj, double
 
 /* Autotuner: runs `sample` (device coordinates) under candidate launch shapes
    (128/256/512 threads per block, full and half occupancy) with the automatic
-   iteration choice, then the fastest shape with the short and the long
-   iteration (pdd_ctx_set_iteration; FP32 paths), times each with CUDA events
-   on the context's stream, and keeps the fastest as the context's launch
-   shape and iteration.  Outputs (nullable): the chosen shape and its time
-   (pdd_ctx_get_launch gives the iteration).  Results of later calls do not
-   depend on the choice.                                                     */
+   iteration and claim, then the fastest shape with the short and the long
+   iteration (pdd_ctx_set_iteration; FP32 paths), then with claims of 1, 4 and
+   16 paths per lane (pdd_ctx_set_claim), times each with CUDA events on the
+   context's stream, and keeps the fastest as the context's launch shape,
+   iteration and claim.  Outputs (nullable): the chosen shape and its time
+   (pdd_ctx_get_launch gives the iteration, pdd_ctx_get_claim the claim).
+   Results of later calls do not depend on the choice.                       */
 int pdd_autotune(pdd_problem* problem, const pdd_estimate_args* sample, int* best_threads,
                  int* best_max_blocks, double* best_ms);
 
@@ -511,7 +526,7 @@ typedef struct {
                                   (PDD_ERR_DEADLINE) a request whose predicted path-steps,
                                   added to the predicted remaining path-steps of every
                                   queued and running request, would take longer than
-                                  0.9 x deadline_s at the server's measured rate (the rest
+                                  0.8 x deadline_s at the server's measured rate (the rest
                                   is a margin for the error of the predicted work and rate;
                                   a guarantee under PDD_SERVE_EARLIEST_DEADLINE as far as the
                                   predictions hold, an estimate under the other policies);

@@ -87,6 +87,7 @@ struct pdd_ctx {
   int block_threads = 0;  // launch shape (0: defaults), set by pdd_ctx_set_launch / pdd_autotune
   int max_blocks = 0;
   int iter_mode = PDD_ITER_AUTO;  // steps per iteration (pdd_ctx_set_iteration / pdd_autotune)
+  int claim = 0;  // paths per lane per cursor claim, 0 = automatic (pdd_ctx_set_claim)
   cudaGraphExec_t gexec = nullptr;  // cached graph of the last PDD_FLAG_GRAPH call
   uint64_t gkey = 0;
   int64_t graph_captures = 0;
@@ -139,6 +140,7 @@ bool ctx_view(pdd_ctx* c, int* device, int* num_sms, int* block_threads, int* ma
 }
 pdd_ctx* problem_ctx(pdd_problem* p) { return p ? p->ctx : nullptr; }
 int ctx_iter_mode(pdd_ctx* c) { return c ? c->iter_mode : PDD_ITER_AUTO; }
+int ctx_claim(pdd_ctx* c) { return c ? c->claim : 0; }
 }  // namespace pdd
 
 namespace pdd {
@@ -353,6 +355,7 @@ static int estimate_impl(pdd_problem* p, int n_levels, const pdd_estimate_args* 
   pa.max_blocks = c->max_blocks;
   pa.block_threads = c->block_threads;
   pa.iter_mode = c->iter_mode;
+  pa.claim = c->claim;
   const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
   uint32_t rec_base[PDD_MAX_LEVELS];
   {
@@ -934,6 +937,7 @@ int pdd_accumulate(pdd_problem* p, const pdd_estimate_args* a, uint64_t path_off
   pa.max_blocks = c->max_blocks;
   pa.block_threads = c->block_threads;
   pa.iter_mode = c->iter_mode;
+  pa.claim = c->claim;
   pa.n_segs = 1;
   SegArgs& sg = pa.seg[0];
   const int dim = p->dim;
@@ -1067,6 +1071,7 @@ static int coupled_launch(pdd_problem* p, const pdd_estimate_args* a, const Leve
   pa.max_blocks = c->max_blocks;
   pa.block_threads = c->block_threads;
   pa.iter_mode = c->iter_mode;
+  pa.claim = c->claim;
   pa.n_segs = 2;
   pa.total = (unsigned long long)n * (unsigned long long)a->n_paths;
   const double c0 = p->desc.exit_rule == PDD_EXIT_GOBET_MENOZZI ? 0.5826 : 0.0;
@@ -1243,6 +1248,27 @@ int pdd_ctx_set_iteration(pdd_ctx* c, int mode) {
   return PDD_OK;
 }
 
+int pdd_ctx_set_claim(pdd_ctx* c, int paths_per_lane) {
+  if (!c || paths_per_lane < 0 || paths_per_lane > 64 ||
+      (paths_per_lane & (paths_per_lane - 1)) != 0) {
+    set_error("pdd_ctx_set_claim: NULL context or paths_per_lane not 0 or a power of two <= 64");
+    return PDD_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->claim = paths_per_lane;
+  return PDD_OK;
+}
+
+int pdd_ctx_get_claim(pdd_ctx* c, int* paths_per_lane) {
+  if (!c || !paths_per_lane) {
+    set_error("pdd_ctx_get_claim: NULL argument");
+    return PDD_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(c->mu);
+  *paths_per_lane = c->claim;
+  return PDD_OK;
+}
+
 int pdd_ctx_get_launch(pdd_ctx* c, int* block_threads, int* max_blocks, int* iteration) {
   if (!c) {
     set_error("pdd_ctx_get_launch: NULL context");
@@ -1283,7 +1309,7 @@ int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_thre
   out.mean_phi = dmean;
   pdd_estimate_args a = *sample;
   a.flags &= ~(PDD_FLAG_EMIT_PATHS | PDD_FLAG_ASYNC);
-  const int old_iter = c->iter_mode;
+  const int old_iter = c->iter_mode, old_claim = c->claim;
   int rc = PDD_OK;
   // CUDA-event time of the sample under the context's current settings (the
   // first of two runs warms up)
@@ -1315,6 +1341,7 @@ int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_thre
   int bt = 0, bb = 0, bi = PDD_ITER_AUTO;
   double bms = 1e300;
   pdd_ctx_set_iteration(c, PDD_ITER_AUTO);
+  pdd_ctx_set_claim(c, 0);
   for (int ti = 0; ti < 3 && rc >= 0; ++ti) {
     // full occupancy, and half of it (fewer resident warps, less L1 pressure)
     for (int frac = 0; frac < 2 && rc >= 0; ++frac) {
@@ -1346,6 +1373,20 @@ int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_thre
       }
     }
   }
+  // paths per lane per cursor claim (the automatic choice was timed above)
+  int bc = 0;
+  if (rc >= 0) {
+    pdd_ctx_set_launch(c, bt, bb);
+    pdd_ctx_set_iteration(c, bi);
+    for (int claim : {1, 4, 16}) {
+      pdd_ctx_set_claim(c, claim);
+      const double ms = time_one();
+      if (rc >= 0 && ms < bms) {
+        bms = ms;
+        bc = claim;
+      }
+    }
+  }
   {
     DeviceGuard g(c->device);
     cudaFree(dmean);
@@ -1353,10 +1394,12 @@ int pdd_autotune(pdd_problem* p, const pdd_estimate_args* sample, int* best_thre
   if (rc < 0) {
     pdd_ctx_set_launch(c, old_threads, old_blocks);
     pdd_ctx_set_iteration(c, old_iter);
+    pdd_ctx_set_claim(c, old_claim);
     return rc;
   }
   pdd_ctx_set_launch(c, bt, bb);
   pdd_ctx_set_iteration(c, bi);
+  pdd_ctx_set_claim(c, bc);
   if (best_threads) *best_threads = bt;
   if (best_max_blocks) *best_max_blocks = bb;
   if (best_ms) *best_ms = bms;

@@ -26,7 +26,7 @@ constexpr unsigned kErrBoundsAll = 62u;
 #endif
 constexpr int kAccWords = 16;               // 64-bit words per node record
 static_assert(kAccWords == PDD_RECORD_WORDS, "node record size");
-constexpr unsigned long long kWarpBatch = 32;  // path indices a warp takes per cursor grab
+constexpr unsigned long long kWarpBatch = 32;  // path indices of a warp claim per path per lane
 
 constexpr int kMaxSegments = 128;          // segments (levels / requests) per launch
 // Launches whose segments hold at most this many node records in total keep a
@@ -72,6 +72,8 @@ struct PathArgs {
   int max_blocks;              // 0 = occupancy x SM count
   int block_threads;           // 0 = default (256)
   int iter_mode;               // Euler steps per iteration: PDD_ITER_AUTO / _SHORT / _LONG
+  int claim;                   // paths per lane a warp claims from the cursor at once (0: auto)
+  unsigned long long warp_batch;  // kWarpBatch x the resolved claim; set by the launcher
   int n_segs;                  // 1 .. kMaxSegments; segments in increasing `begin`
   uint32_t cache_nodes;        // record slots cached in shared memory per block (0: none);
                                // set by the launchers
@@ -135,6 +137,7 @@ int error_word_status(unsigned err, const char* who);
 bool problem_view(pdd_problem* p, ProblemView* v);
 bool ctx_view(pdd_ctx* c, int* device, int* num_sms, int* block_threads, int* max_blocks);
 int ctx_iter_mode(pdd_ctx* c);  // the context's PDD_ITER_* choice
+int ctx_claim(pdd_ctx* c);      // the context's paths-per-lane claim (0: automatic)
 pdd_ctx* problem_ctx(pdd_problem* p);
 
 cudaError_t launch_paths(int kind, int precision, int cv, const PathArgs& a, int num_sms,

@@ -165,6 +165,7 @@ extern "C" int pdd_estimate_nodes_noalloc(pdd_problem* problem, const pdd_estima
   pa.max_blocks = max_blocks;
   pa.block_threads = block_threads;
   pa.iter_mode = ctx_iter_mode(problem_ctx(problem));
+  pa.claim = ctx_claim(problem_ctx(problem));
   pa.n_segs = 1;
   SegArgs& sg = pa.seg[0];
   sg.cx = a->coords[0];

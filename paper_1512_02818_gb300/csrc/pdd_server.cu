@@ -21,7 +21,7 @@
 // pilot launch the first time the pair is seen and refined by every
 // completed request; with a deadline set, pdd_submit refuses a request whose
 // work, after the predicted remaining work of everything queued and running,
-// would not finish within 90 % of the deadline at the measured rate
+// would not finish within 80 % of the deadline at the measured rate
 // (path-steps of retired launches over the time they took).  Under the earliest-deadline
 // policy (every request has the same relative deadline, so it serves them in
 // submission order) the admitted work finishes in time as far as the
@@ -252,10 +252,13 @@ double backlog_work(pdd_server* s) {
 }
 
 // Share of the deadline that admission fills with predicted work; the rest
-// is a margin for the error of the predicted work and rate (exit-index
-// estimates from a pilot, the measured rate's drift with the request mix,
-// host gaps between launches).
-constexpr double kDeadlineShare = 0.9;
+// is a margin for the error of the predicted work and rate: work is counted
+// in path-steps and the rate is the average over the requests served, while
+// a control-variate step costs ~1.3 plain ones and 10-step paths run at
+// about half the path-step rate of 1,000-step ones, so a stretch of costly
+// requests runs slower than the average (at 90 % the p99 latency under
+// overload was 1-7 % above the deadline).
+constexpr double kDeadlineShare = 0.8;
 
 // Path-steps per second of GPU-busy time over every retired launch (launch
 // overheads and the drain of small launches included), once 0.2 s of busy
@@ -459,6 +462,7 @@ bool issue_launch(pdd_server* s) {
   ctx_view(s->ctx, &dev, &sms, &bt, &mb);
   pa.block_threads = bt;
   pa.max_blocks = mb;
+  pa.claim = ctx_claim(s->ctx);
   unsigned long long begin = 0;
   int ns = 0;
   Launch L;

@@ -158,6 +158,8 @@ _SIGS = [
     ("pdd_ctx_set_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     ("pdd_ctx_abort", ctypes.c_int, [ctypes.c_void_p]),
     ("pdd_ctx_set_iteration", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("pdd_ctx_set_claim", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("pdd_ctx_get_claim", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
     ("pdd_ctx_get_launch", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
@@ -559,6 +561,15 @@ class Context:
     def set_iteration(self, mode: int) -> None:
         """Euler steps per iteration: PDD_ITER_AUTO / _SHORT / _LONG."""
         _check(self._lib.pdd_ctx_set_iteration(self.handle, mode))
+
+    def set_claim(self, paths_per_lane: int) -> None:
+        """Paths per lane a warp claims from the cursor at once (0: automatic)."""
+        _check(self._lib.pdd_ctx_set_claim(self.handle, paths_per_lane))
+
+    def get_claim(self) -> int:
+        v = ctypes.c_int()
+        _check(self._lib.pdd_ctx_get_claim(self.handle, ctypes.byref(v)))
+        return v.value
 
     def get_launch(self) -> tuple[int, int, int]:
         """(block_threads, max_blocks, iteration mode) of the context."""

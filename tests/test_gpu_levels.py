@@ -130,6 +130,12 @@ def test_launch_shape_and_autotuner_do_not_change_results(env):
     for mode in (pdd.PDD_ITER_SHORT, pdd.PDD_ITER_LONG, pdd.PDD_ITER_AUTO):
         ctx.set_iteration(mode)
         _same(pdd, ref, prob.estimate(nodes, 900, 1e-3, grid_id=0))
+    # paths per lane claimed from the cursor at once
+    for claim in (1, 2, 16, 64, 0):
+        ctx.set_claim(claim)
+        assert ctx.get_claim() == claim
+        _same(pdd, ref, prob.estimate(nodes, 900, 1e-3, grid_id=0))
+        _same(pdd, ref, prob.estimate(nodes, 900, 1e-3, grid_id=0))
     p3 = pdd.Problem(ctx, pdd.PDD_PROBLEM_CUBE_3D)
     p3.set_control_grid(0, W.control_grid(2, 33, 1e-2))
     n3 = W.workload_nodes("c2")[::97]
@@ -137,6 +143,9 @@ def test_launch_shape_and_autotuner_do_not_change_results(env):
     for mode in (pdd.PDD_ITER_SHORT, pdd.PDD_ITER_LONG):
         ctx.set_iteration(mode)
         _same(pdd, ref3, p3.estimate(n3, 300, 1e-3, grid_id=0))
+    ctx.set_claim(8)
+    _same(pdd, ref3, p3.estimate(n3, 300, 1e-3, grid_id=0))
+    ctx.set_claim(0)
     ctx.set_iteration(pdd.PDD_ITER_AUTO)
     p3.close()
     t, b, ms = prob.autotune(nodes, 900, 1e-3, grid_id=0)
@@ -148,8 +157,13 @@ def test_launch_shape_and_autotuner_do_not_change_results(env):
         ctx.set_launch(100, 0)
     with pytest.raises(pdd.PddError):
         ctx.set_iteration(7)
+    for bad in (-1, 3, 128):
+        with pytest.raises(pdd.PddError):
+            ctx.set_claim(bad)
+    assert ctx.get_claim() in (0, 1, 4, 16)
     ctx.set_launch(0, 0)
     ctx.set_iteration(pdd.PDD_ITER_AUTO)
+    ctx.set_claim(0)
     prob.close()
 
 
