@@ -611,8 +611,9 @@ void pdd_server_destroy(pdd_server* server);
      mode: none, grid or exact) -- loads that kernel, and loading can reserve
      device memory.  Warm up once per variant (any call, e.g. with few paths)
      before relying on the call allocating nothing.
-   - The launch shape is the context's (pdd_ctx_set_launch / pdd_autotune), as
-     for pdd_estimate_nodes; the caller's current device is left unchanged.
+   - The launch settings are the context's (shape, iteration and claim:
+     pdd_ctx_set_launch / _set_iteration / _set_claim / pdd_autotune), as for
+     pdd_estimate_nodes; the caller's current device is left unchanged.
    - Every call uses the same array, which keeps the previous call's contents
      (each call clears what must start at zero).  Calls that can overlap on
      the GPU -- different streams or different contexts -- race on it and give
