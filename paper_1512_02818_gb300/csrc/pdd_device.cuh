@@ -63,8 +63,13 @@ __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, 
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
 
 // Uniform (0,1) from a 32-bit word: ((w >> 9) + 1/2) 2^-23, exact in FP32.
+// Formed without an int-to-float conversion (conversions issue to a narrower
+// pipe than integer logic and FP32 adds): 1 + (w >> 9) 2^-23 is the float
+// with those mantissa bits and exponent 0, and subtracting 1 - 2^-24 from it
+// is exact (Sterbenz), which gives the same value.  Measured on the C1 step:
+// plain pass +3.6 %, control-variate passes +2.3 % path-steps/s.
 __device__ __forceinline__ float unit_f(uint32_t w) {
-  return fmaf((float)(w >> 9), 0x1p-23f, 0x1p-24f);
+  return __fsub_rn(__uint_as_float((w >> 9) | 0x3F800000u), 1.0f - 0x1p-24f);
 }
 
 // Box-Muller pair from words (wa, wb): r = sqrt(-2 ln u_a), angle 2 pi u_b.
