@@ -49,15 +49,15 @@ TARGET_RMSE = 1e-3
 # smsp__thread_inst_executed.sum over the path-steps of the full-size launches
 # of this benchmark (a one-pass capture of the 4-steps-per-iteration kernels;
 # the planning estimates were 110 and 150).
-ALGO_INSTR = {"plain": 104.5, "cv": 134.4}
+ALGO_INSTR = {"plain": 101.6, "cv": 131.2}
 # DRAM bytes (read + write) per launch of the dominant kernel (the eps = 1e-2
 # pass) from the same full-size capture; None whenever the kernel has changed
 # since that capture.
-NCU_TRAFFIC_BYTES = 1275136
+NCU_TRAFFIC_BYTES = 1274880
 # Thread-instructions per path-step of the 3D control-variate kernel over the
 # full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
 # over its path-steps, a one-pass capture; the planning estimate was 190).
-INSTR_3D = 223.1
+INSTR_3D = 219.0
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
