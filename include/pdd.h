@@ -212,7 +212,8 @@ int pdd_ctx_graph_count(pdd_ctx* ctx, int64_t* captures);
 int pdd_ctx_set_launch(pdd_ctx* ctx, int block_threads, int max_blocks);
 /* Euler steps a path kernel takes per iteration, between lane refills (the
    scheduling quantum): PDD_ITER_SHORT = 2 in 2D / 4 in 3D, PDD_ITER_LONG =
-   4 / 8 (FP32 paths; FP64 paths always take the short one), PDD_ITER_AUTO
+   4 (8 without a control variate) in 2D / 8 in 3D (FP32 paths; FP64 paths
+   always take the short one), PDD_ITER_AUTO
    (the default) = long when the segments with time steps above 2e-3 hold at
    most 5 % of the launch's expected path-steps (n_nodes x n_paths / h), short
    otherwise.  Longer iterations pay the refill and exit bookkeeping once per

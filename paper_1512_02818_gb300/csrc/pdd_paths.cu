@@ -44,7 +44,8 @@ constexpr int kMaxBlockThreads = 512;  // largest block size a launch may ask fo
 #endif
 constexpr unsigned kFull = 0xFFFFFFFFu;
 // Euler steps per iteration of the path kernels (between lane refills and
-// exit parking): 4 in 2D (two Philox blocks) and 8 in 3D (six) halve the
+// exit parking): 4 in 2D (two Philox blocks; 8 for the plain estimator, see
+// LongSteps2D) and 8 in 3D (six) halve the
 // per-step share of the refill, ring and loop work against 2 and 4, but a
 // lane whose path ends early in an iteration idles for the rest of it, which
 // costs on short paths.  A launch takes the longer iterations when segments
@@ -52,6 +53,14 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // kShortWorkShare of its expected path-steps (n_nodes x n_paths / h per
 // segment).
 constexpr double kLongPathH = 2e-3;
+// The long 2D iteration: eight steps (four Philox blocks) for the plain
+// estimator, whose step is short enough that the refill and ring bookkeeping
+// still weigh (+3 % path-steps/s against four), and four with a control
+// variate (eight measured no faster).
+template <class T, int CV>
+struct LongSteps2D {
+  static constexpr int value = sizeof(T) == 4 ? (CV == 0 ? 8 : 4) : 2;
+};
 constexpr double kShortWorkShare = 0.05;
 enum { kCvNone = 0, kCvGrid = 1, kCvExact = 2 };
 
@@ -1238,7 +1247,7 @@ static cudaError_t launch_one(const PathArgs& a, int num_sms, cudaStream_t st, i
   } else if (longer) {
     static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
     static std::atomic<int> attr{0};
-    return launch_persistent(paths_2d<P, T, CV, MULTI, sizeof(T) == 4 ? 4 : 2>, a, num_sms, st,
+    return launch_persistent(paths_2d<P, T, CV, MULTI, LongSteps2D<T, CV>::value>, a, num_sms, st,
                              blocks, ExitRing<T, 2>::kBytes, &attr, per_sm);
   } else {
     static std::atomic<int> per_sm[kMaxBlockThreads / 32 + 1];
@@ -1254,7 +1263,7 @@ static cudaError_t occupancy_one(int threads, int* occ) {
   if constexpr (P::kDim == 3)
     kern = paths_3d<P, T, CV, MULTI, sizeof(T) == 4 ? 8 : 4>;
   else
-    kern = paths_2d<P, T, CV, MULTI, sizeof(T) == 4 ? 4 : 2>;
+    kern = paths_2d<P, T, CV, MULTI, LongSteps2D<T, CV>::value>;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       occ, kern, threads, (size_t)(threads / 32) * ExitRing<T, P::kDim>::kBytes);
 }
