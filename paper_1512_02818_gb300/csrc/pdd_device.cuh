@@ -112,9 +112,6 @@ struct Coef {
   T b0, b1, b2, c, f, g0, g1, g2, sa;
 };
 
-#ifndef PDD_EVAL_FACTORED
-#define PDD_EVAL_FACTORED 1
-#endif
 // u = e^{x+y} cos(x-y); Delta u = 0.  Without the gradient (GRAD: the exact
 // control variate) f is formed with the common factor e^{x+y} taken out, two
 // multiplies fewer per step (C1 plain pass +2 %, control variate +0.7 %).
@@ -125,25 +122,29 @@ __device__ __forceinline__ void exp_cos_2d(T x, T y, Coef<T>& o, T& u) {
   T sn, cs;
   m_sincos(sub_rn(x, y), &sn, &cs);
   u = mul_rn(E, cs);
-  o.b0 = mul_rn(T(0.5), sy);
-  o.b1 = mul_rn(T(0.5), cx);
+  // b = (sin y, cos x) / 2 is returned without the 1/2 (kDriftHalf: the
+  // Euler step multiplies it by h/2, which is exact, so X is unchanged)
+  o.b0 = sy;
+  o.b1 = cx;
   o.b2 = T(0);
   o.c = fma_rn(y, y, fma_rn(x, x, T(1)));  // 1 + x^2 + y^2
   const T d1 = sub_rn(cs, sn), d2 = add_rn(cs, sn);  // grad u = E (d1, d2)
-  if (GRAD || !PDD_EVAL_FACTORED) {
+  if (GRAD) {
     const T ux = mul_rn(E, d1), uy = mul_rn(E, d2);
-    o.f = fma_rn(o.b1, uy, fma_rn(o.b0, ux, mul_rn(-o.c, u)));  // b . grad u - c u
+    // b . grad u - c u
+    o.f = fma_rn(T(0.5), fma_rn(cx, uy, mul_rn(sy, ux)), mul_rn(-o.c, u));
     o.g0 = ux;
     o.g1 = uy;
   } else {
     // the same with the common factor E taken out: E (b . (d1, d2) - c cs)
-    o.f = mul_rn(E, fma_rn(o.b1, d2, fma_rn(o.b0, d1, mul_rn(-o.c, cs))));
+    o.f = mul_rn(E, fma_rn(T(0.5), fma_rn(cx, d2, mul_rn(sy, d1)), mul_rn(-o.c, cs)));
     o.g0 = o.g1 = T(0);
   }
   o.g2 = T(0);
 }
 
 struct Cfg0 {
+  static constexpr bool kDriftHalf = true;  // eval returns 2 b
   static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 2;
   static constexpr bool kAniso = false;
@@ -163,6 +164,7 @@ struct Cfg0 {
 };
 
 struct Aniso {
+  static constexpr bool kDriftHalf = true;  // eval returns 2 b
   static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 2;
   static constexpr bool kAniso = true;
@@ -191,6 +193,7 @@ struct Aniso {
 };
 
 struct Cube3 {
+  static constexpr bool kDriftHalf = false;
   static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 3;
   static constexpr bool kAniso = false;
@@ -228,6 +231,7 @@ struct Cube3 {
 // The paper's example PDE (Sec. 6): sigma = sqrt(2) I, b = cos(x+y)/(1.1+sin(x+y)) [1,1],
 // c = (x^2+y^2)/(1.1+sin(x+y)), u = 2 cos(2(y-2)x) + sin(3(x-2)y) + 3.1.
 struct PaperEx {
+  static constexpr bool kDriftHalf = false;
   static constexpr int kDim = 2;
   static constexpr bool kAniso = false;
   static constexpr bool kIsoScaled = true;  // sigma = sa * I with sa = sqrt(2)
@@ -266,6 +270,7 @@ struct PaperEx {
 };
 
 struct Harmonic {
+  static constexpr bool kDriftHalf = false;
   static constexpr bool kIsoScaled = false;
   static constexpr int kDim = 2;
   static constexpr bool kAniso = false;

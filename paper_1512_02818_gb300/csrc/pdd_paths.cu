@@ -235,9 +235,12 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
     kahan_add(s.XI, s.XIc, -s.Y, dot);
   }
   if (!P::kUnitY) kahan_add(s.Z, s.Zc, mul_rn(-h, s.Y), o.f);
-  s.x[0] = add_rn(s.x[0], fma_rn(h, o.b0, sdW[0]));
-  s.x[1] = add_rn(s.x[1], fma_rn(h, o.b1, sdW[1]));
-  if (D == 3) s.x[2] = add_rn(s.x[2], fma_rn(h, o.b2, sdW[2]));
+  // the drift's step: h b, or (h/2)(2 b) for problems whose eval returns 2 b
+  // (the same product: halving h is exact)
+  const T hb = P::kDriftHalf ? mul_rn(T(0.5), h) : h;
+  s.x[0] = add_rn(s.x[0], fma_rn(hb, o.b0, sdW[0]));
+  s.x[1] = add_rn(s.x[1], fma_rn(hb, o.b1, sdW[1]));
+  if (D == 3) s.x[2] = add_rn(s.x[2], fma_rn(hb, o.b2, sdW[2]));
   if (!P::kUnitY)
     s.Y = mul_rn(s.Y, (YRULE && a.y_exp) ? m_exp(mul_rn(-h, o.c)) : fma_rn(-h, o.c, T(1)));
   s.k += 1;
