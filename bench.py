@@ -53,7 +53,7 @@ ALGO_INSTR = {"plain": 95.7, "cv": 128.3}
 # DRAM bytes (read + write) per launch of the dominant kernel (the eps = 1e-2
 # pass) from the same full-size capture; None whenever the kernel has changed
 # since that capture.
-NCU_TRAFFIC_BYTES = 1364224
+NCU_TRAFFIC_BYTES = None
 # Thread-instructions per path-step of the 3D control-variate kernel over the
 # full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
 # over its path-steps, a one-pass capture; the planning estimate was 190).

@@ -158,12 +158,22 @@ __device__ __forceinline__ void start_path(const PathArgs& a, unsigned long long
   if (MULTI) load_seg<T, D>(sg, ls);
 }
 
+#ifndef PDD_EXIT_CENTRED
+#define PDD_EXIT_CENTRED 1
+#endif
 // Finish test of Algorithm 1: d(X_k) >= -c0 |sigma^T N| sqrt(h).
 template <class P, class T, int D>
 __device__ __forceinline__ bool should_finish(const PathState<T>& s, T thr0) {
-  const T m = (D == 3) ? face_distance(s.x[0], s.x[1], s.x[2]) : face_distance(s.x[0], s.x[1]);
   T thr = thr0;
   if (P::kAniso || P::kIsoScaled) thr = mul_rn(thr, P::template exit_scale<T>(s.x[0], s.x[1], s.x[2]));
+  if (sizeof(T) == 4 && PDD_EXIT_CENTRED) {
+    // FP32: the distance to the unit box's faces is 1/2 - max_i |X_i - 1/2|,
+    // one instruction fewer than the minimum over the 2D faces
+    T e = fmaxf(fabsf(sub_rn(s.x[0], T(0.5))), fabsf(sub_rn(s.x[1], T(0.5))));
+    if (D == 3) e = fmaxf(e, fabsf(sub_rn(s.x[2], T(0.5))));
+    return e >= sub_rn(T(0.5), thr);
+  }
+  const T m = (D == 3) ? face_distance(s.x[0], s.x[1], s.x[2]) : face_distance(s.x[0], s.x[1]);
   return m <= thr;
 }
 
@@ -234,7 +244,9 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
     if (D == 3) dot = fma_rn(gv[2], sdW[2], dot);
     kahan_add(s.XI, s.XIc, -s.Y, dot);
   }
-  if (!P::kUnitY) kahan_add(s.Z, s.Zc, mul_rn(-h, s.Y), o.f);
+  // h Y_k serves the Z increment and the Euler rule Y_k (1 - h c) = Y_k - (h Y_k) c
+  const T hY = P::kUnitY ? T(0) : mul_rn(h, s.Y);
+  if (!P::kUnitY) kahan_add(s.Z, s.Zc, -hY, o.f);
   // the drift's step: h b, or (h/2)(2 b) for problems whose eval returns 2 b
   // (the same product: halving h is exact)
   const T hb = P::kDriftHalf ? mul_rn(T(0.5), h) : h;
@@ -242,7 +254,7 @@ __device__ __forceinline__ void euler_step(const PathArgs& a, PathState<T>& s,
   s.x[1] = add_rn(s.x[1], fma_rn(hb, o.b1, sdW[1]));
   if (D == 3) s.x[2] = add_rn(s.x[2], fma_rn(hb, o.b2, sdW[2]));
   if (!P::kUnitY)
-    s.Y = mul_rn(s.Y, (YRULE && a.y_exp) ? m_exp(mul_rn(-h, o.c)) : fma_rn(-h, o.c, T(1)));
+    s.Y = (YRULE && a.y_exp) ? mul_rn(s.Y, m_exp(mul_rn(-h, o.c))) : fma_rn(-hY, o.c, s.Y);
   s.k += 1;
 }
 
