@@ -49,11 +49,11 @@ TARGET_RMSE = 1e-3
 # smsp__thread_inst_executed.sum over the path-steps of the full-size launches
 # of this benchmark (a one-pass capture of the 4-steps-per-iteration kernels;
 # the planning estimates were 110 and 150).
-ALGO_INSTR = {"plain": 95.7, "cv": 128.3}
+ALGO_INSTR = {"plain": 93.7, "cv": 126.4}
 # DRAM bytes (read + write) per launch of the dominant kernel (the eps = 1e-2
 # pass) from the same full-size capture; None whenever the kernel has changed
 # since that capture.
-NCU_TRAFFIC_BYTES = None
+NCU_TRAFFIC_BYTES = 1364224
 # Thread-instructions per path-step of the 3D control-variate kernel over the
 # full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
 # over its path-steps, a one-pass capture; the planning estimate was 190).
