@@ -56,8 +56,10 @@ ALGO_INSTR = {"plain": 93.7, "cv": 126.4}
 NCU_TRAFFIC_BYTES = 1364224
 # Thread-instructions per path-step of the 3D control-variate kernel over the
 # full-size cascade launch of --workload c2 (ncu smsp__thread_inst_executed.sum
-# over its path-steps, a one-pass capture; the planning estimate was 190).
-INSTR_3D = 219.0
+# over its path-steps, a one-pass capture; the planning estimate was 190), for
+# the short (4 steps per iteration) and the long (8) iteration the autotuner
+# may pick.
+INSTR_3D = {"short": 222.7, "long": None}
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
@@ -90,6 +92,8 @@ def parse_args():
     ap.add_argument("--a0", type=float, default=1e-3, help="cascade: nodal target tolerance")
     ap.add_argument("--window", type=float, default=10.0, help="c3: arrival window (s)")
     ap.add_argument("--rate", type=float, default=200.0, help="c3: arrivals per second")
+    ap.add_argument("--iteration", choices=["tuned", "auto", "short", "long"], default="tuned",
+                    help="c2: steps per iteration (default: the autotuner's choice)")
     ap.add_argument("--deadline", type=float, default=10.0,
                     help="c3: admission deadline (s) of the server at the offered rate")
     return ap.parse_args()
@@ -608,6 +612,13 @@ def run_c2(args):
         sub = [torch.from_numpy(np.ascontiguousarray(nodes[::8, j])).to(dev) for j in range(3)]
         tuned = prob.autotune(sub, levels_cfg[2]["n_paths"] // (10 * div), levels_cfg[2]["dt"],
                               grid_id=2, stream_tag=77)
+    if args.iteration != "tuned":
+        ctx.set_iteration({"auto": pdd.PDD_ITER_AUTO, "short": pdd.PDD_ITER_SHORT,
+                           "long": pdd.PDD_ITER_LONG}[args.iteration])
+    # the cascade's auto rule takes the long iteration (its short-path level
+    # holds 0.02 % of the path-steps)
+    iter_run = {0: "long", 1: "short", 2: "long"}[ctx.get_launch()[2]]
+    instr_3d = INSTR_3D[iter_run]
 
     def step():
         pdd.pdd_estimate_levels(prob.handle, largs, louts, pdd.PDD_FLAG_GRAPH | pdd.PDD_FLAG_ASYNC)
@@ -654,15 +665,17 @@ def run_c2(args):
             "levels": per_level, "graph_captures": ctx.graph_count(),
             "gpu_launches": int(launches), "clocks": clk, "cpu_baseline": cpu,
             "roofline": {"bound": "alu", "unit": "T thread-instr/s",
-                         "achieved": INSTR_3D * value / 1e12,
+                         "achieved": instr_3d * value / 1e12 if instr_3d else None,
                          "peak": torch.cuda.get_device_properties(0).multi_processor_count
                          * 4 * 32 * 2.070e9 / 1e12,
-                         "algorithmic": f"{INSTR_3D} thread-instr per 3D control-variate "
-                                        "path-step (ncu, executed, full-size cascade launch)",
+                         "algorithmic": f"{instr_3d} thread-instr per 3D control-variate "
+                                        f"path-step ({iter_run} iteration; ncu, executed, "
+                                        "full-size cascade launch)",
                          "second_limit": "L1 data pipe: 78 % of its peak in the ncu capture of "
                                          "the profiling case (two 256-bit cell-record gathers "
                                          "per step), issue 75 %"}}
-    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
+    line["roofline"]["frac"] = (line["roofline"]["achieved"] / line["roofline"]["peak"]
+                                if instr_3d else None)
     prob.close()
     ctx.close()
     return line
