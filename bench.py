@@ -59,7 +59,7 @@ NCU_TRAFFIC_BYTES = 1364224
 # over its path-steps, a one-pass capture; the planning estimate was 190), for
 # the short (4 steps per iteration) and the long (8) iteration the autotuner
 # may pick.
-INSTR_3D = {"short": 222.7, "long": None}
+INSTR_3D = {"short": 222.7, "long": 217.0}
 WORKLOAD = ("2D CFG0 (b=(sin y/2, cos x/2), c=1+x^2+y^2, u=e^{x+y}cos(x-y)), 2x2 subdomains, "
             "256 interfacial nodes x 1e5 paths, dt=1e-4, Gobet-Menozzi; plain + control "
             "variate on 129^2 grids eps in {1e-1,1e-2,1e-3}")
